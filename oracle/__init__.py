@@ -1,0 +1,133 @@
+"""Oracle: a plain, slow FP64 CPU scorer for Beagle population fitness.
+
+TEST INFRASTRUCTURE ONLY. It is loaded by the tests, by the package's ``smoke()`` check and
+by the benchmark's CPU-baseline leg, and by nothing on the product path. It shares no code
+with the CUDA path; see ``oracle.c`` for what it computes and which passages it follows.
+
+Pins (tests/test_oracle_*.py): the paper's two worked genomes against the closed-form
+quadratic root (Section 3.3); per-opcode values by hand (Table 3); closed-form MSE;
+1 - r^2 against numpy's correlation and a least-squares fit; invariance under permuting
+cases; brute force over every program up to length 5 on a tiny alphabet against an exact
+rational evaluator built on a different algorithm (tree reconstruction).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+
+FP64, FP32 = 0, 1
+F_INVALID, F_DEGENERATE, F_MALFORMED, F_NEAR = 1, 2, 4, 256
+STACK = 32
+CHECK_ERRORS = {0: "ok", 1: "underflow", 2: "overflow", 3: "final depth", 4: "opcode",
+                5: "variable", 6: "empty"}
+
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile oracle.c into liboracle.so (gcc, OpenMP, no fast-math, no FP contraction)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp",
+                               "-ffp-contract=off", "-fno-fast-math", _SRC, "-o", tmp, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        L = ctypes.CDLL(_LIB)
+        P = ctypes.c_void_p
+        L.oracle_check_program.argtypes = [P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]
+        L.oracle_check_program.restype = ctypes.c_int
+        L.oracle_eval.argtypes = [P, P, ctypes.c_int32, P, ctypes.c_int64, ctypes.c_int32,
+                                  ctypes.c_int32, P]
+        L.oracle_eval.restype = ctypes.c_uint32
+        L.oracle_aggregate.argtypes = [P, P, ctypes.c_int64, ctypes.c_uint32, P, P, P]
+        L.oracle_aggregate.restype = None
+        L.oracle_score.argtypes = [P, P, P, P, ctypes.c_int64, P, P, ctypes.c_int64,
+                                   ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, P, P, P]
+        L.oracle_score.restype = ctypes.c_int
+        L.oracle_threads.restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def _p(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _mode(mode) -> int:
+    if mode in (FP64, "fp64"):
+        return FP64
+    if mode in (FP32, "fp32"):
+        return FP32
+    raise ValueError(mode)
+
+
+def threads() -> int:
+    return int(lib().oracle_threads())
+
+
+def check_program(ops, d: int, max_depth: int = STACK) -> int:
+    ops = np.ascontiguousarray(ops, np.uint8)
+    return int(lib().oracle_check_program(_p(ops), len(ops), d, max_depth))
+
+
+def eval_program(ops, consts, X, mode="fp64"):
+    """Outputs of one program on every case: (f float64 [N], flags)."""
+    ops = np.ascontiguousarray(ops, np.uint8)
+    consts = np.ascontiguousarray(consts, np.float32)
+    X = np.ascontiguousarray(X, np.float32)
+    if X.ndim == 1:
+        X = X[None, :]
+    d, N = X.shape
+    f = np.zeros(N, np.float64)
+    fl = lib().oracle_eval(_p(ops), _p(consts), len(ops), _p(X), N, d, _mode(mode), _p(f))
+    return f, int(fl)
+
+
+def aggregate(f, y, flags: int = 0):
+    """(mse, one_minus_r2, flags) of given outputs f against targets y."""
+    f = np.ascontiguousarray(f, np.float64)
+    y = np.ascontiguousarray(y, np.float32)
+    mse, omr2, fl = ctypes.c_double(), ctypes.c_double(), ctypes.c_uint32()
+    lib().oracle_aggregate(_p(f), _p(y), len(y), flags, ctypes.byref(mse), ctypes.byref(omr2),
+                           ctypes.byref(fl))
+    return mse.value, omr2.value, fl.value
+
+
+def score(ops, offsets, lengths, consts, X, y, mode="fp64", nthreads: int = 0):
+    """Score a population: returns (mse [P], one_minus_r2 [P], flags [P])."""
+    ops = np.ascontiguousarray(ops, np.uint8)
+    offsets = np.ascontiguousarray(offsets, np.int64)
+    lengths = np.ascontiguousarray(lengths, np.int32)
+    consts = np.ascontiguousarray(consts, np.float32)
+    X = np.ascontiguousarray(X, np.float32)
+    if X.ndim == 1:
+        X = X[None, :]
+    y = np.ascontiguousarray(y, np.float32)
+    d, N = X.shape
+    P = len(lengths)
+    mse = np.zeros(P, np.float64)
+    omr2 = np.zeros(P, np.float64)
+    flags = np.zeros(P, np.uint32)
+    rc = lib().oracle_score(_p(ops), _p(offsets), _p(lengths), _p(consts), P, _p(X), _p(y), N,
+                            d, _mode(mode), nthreads, _p(mse), _p(omr2), _p(flags))
+    if rc != 0:
+        raise ValueError("oracle_score rejected its arguments")
+    return mse, omr2, flags
+
+
+def score_programs(progs, X, y, mode="fp64", nthreads: int = 0):
+    """Same as ``score`` for any object with ops/offsets/lengths/consts attributes."""
+    return score(progs.ops, progs.offsets, progs.lengths, progs.consts, X, y, mode, nthreads)
