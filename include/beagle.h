@@ -1,0 +1,183 @@
+/*
+ * beagle.h -- C ABI of the GB300 population-scoring library (libbeagle.so).
+ *
+ * What the library computes follows the Beagle tutorial (arXiv 2607.06731):
+ *   - A genome is a GCL program in reverse Polish notation run on a value stack
+ *     (Section 3.2 and Table 3). Unary ops replace the top value; binary ops pop the top b
+ *     and the value below it a and push a (op) b (SUB is a - b, DIV is a / b).
+ *   - The GPU evaluates each program on every fitness case and returns one aggregated
+ *     fitness per program; the CPU keeps the genetic operators (Section 2.4). Genomes go to
+ *     the device once per generation and datasets stay resident (Sections 2.4, 3.6).
+ *   - Fitness is the mean squared error and 1 - r^2, r being the Pearson correlation of
+ *     Eq. 1 between outputs and targets ("The r value is then squared", Section 2.10).
+ *
+ * Readings of points the paper leaves open (the paper's own DIV, LN, SQRT are unprotected):
+ *   pdiv(a, b) = a / b if |b| > 1e-3, else 1;  plog(a) = ln|a| if |a| > 1e-3, else 0;
+ *   psqrt(a) = sqrt|a|.  A program is INVALID when any value it produces is non-finite or
+ *   has |v| > 1e30; an invalid program scores +inf for both fitness values. When a program's
+ *   output is the same on every case, r is undefined and 1 - r^2 is reported as 1
+ *   (flag DEGENERATE). Thresholds are compared in the arithmetic's own precision (the fp32
+ *   value nearest 1e30 and 1e-3 on the FP32 path).
+ *
+ * Conventions for every call:
+ *   - Return value: BEAGLE_OK (0) or a negative BEAGLE_ERR_* code; beagle_last_error()
+ *     returns a message for the calling thread's last failure.
+ *   - "device" pointers are CUDA device (or managed) memory of the current device; "host"
+ *     pointers are ordinary or pinned host memory. The caller owns every buffer it passes;
+ *     the library owns resident datasets (until released) and its serving state.
+ *   - A stream argument is a cudaStream_t cast to void* (NULL = the legacy default stream).
+ *     Scoring calls are asynchronous on that stream unless stated otherwise: results are
+ *     valid once the stream reaches the call's position.
+ *   - Calls are thread-safe.
+ */
+#ifndef BEAGLE_H
+#define BEAGLE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t beagle_status;
+
+#define BEAGLE_OK             0
+#define BEAGLE_ERR_ARG       -1   /* null pointer, bad size, unknown precision */
+#define BEAGLE_ERR_PROGRAM   -2   /* a program failed the structural check */
+#define BEAGLE_ERR_DATASET   -3   /* unknown dataset id, or dataset values rejected */
+#define BEAGLE_ERR_OOM       -4   /* device memory or serving budget exhausted */
+#define BEAGLE_ERR_CUDA      -5   /* a CUDA runtime call failed */
+#define BEAGLE_ERR_TIMEOUT   -6   /* a bounded wait ran out */
+#define BEAGLE_ERR_BUSY      -7   /* resource still in use */
+#define BEAGLE_ERR_LIMIT     -8   /* a size above a documented maximum */
+
+/* ---- Wire format: one byte per token (Table 3 op names; protected forms as above) ---- */
+#define BEAGLE_OP_CONST   0   /* push consts[token] */
+#define BEAGLE_OP_ADD     1
+#define BEAGLE_OP_SUB     2   /* second - top */
+#define BEAGLE_OP_MUL     3
+#define BEAGLE_OP_PDIV    4   /* second / top, protected */
+#define BEAGLE_OP_SIN     5
+#define BEAGLE_OP_COS     6
+#define BEAGLE_OP_EXP     7
+#define BEAGLE_OP_PLOG    8
+#define BEAGLE_OP_PSQRT   9
+#define BEAGLE_OP_SQUARE 10
+#define BEAGLE_OP_DUP    11   /* push a copy of the top */
+#define BEAGLE_OP_SWAP   12   /* exchange the top two */
+#define BEAGLE_OP_DEL    13   /* pop the top */
+#define BEAGLE_OP_LOAD0  32   /* BEAGLE_OP_LOAD0 + k pushes input x_k (k zero-based) */
+
+#define BEAGLE_MAX_VARS    16    /* inputs per dataset (d) */
+#define BEAGLE_MAX_DEPTH   16    /* values on the GPU stack (the paper's StackSize is 32) */
+#define BEAGLE_MAX_LENGTH  256   /* tokens per program */
+
+/* ---- Result flags ---- */
+#define BEAGLE_FLAG_INVALID     1u  /* a value was non-finite or |v| > 1e30: both fitnesses +inf */
+#define BEAGLE_FLAG_DEGENERATE  2u  /* output identical on every case: one_minus_r2 = 1 */
+#define BEAGLE_FLAG_MALFORMED   4u  /* failed the structural check on the device: both +inf */
+#define BEAGLE_FLAG_TIMEOUT     8u  /* a bounded device wait ran out: result not computed */
+
+/* ---- Precision of program arithmetic ---- */
+#define BEAGLE_FP32_COMPENSATED 0   /* fp32 ops; fp32 compensated sums; fp64 cross-tile merge */
+#define BEAGLE_FP64             1   /* every op and sum in fp64 (plain sums) */
+
+/* One aggregated fitness per program (Section 2.4), 24 bytes. */
+typedef struct beagle_fitness {
+    double mse;           /* (1/N) sum_i (f(x_i) - y_i)^2 */
+    double one_minus_r2;  /* 1 - r^2, r from Eq. 1 */
+    uint32_t flags;       /* BEAGLE_FLAG_* */
+    uint32_t reserved;
+} beagle_fitness;
+
+/*
+ * Upload a dataset and keep it resident on the current device (Section 2.4: data is sent
+ * once; Section 3.6: one (inputs, output) point per fitness case).
+ *   X      [d][N] fp32, row k holds input x_k of every case (column-major by case).
+ *   y      [N] fp32 targets.
+ *   N >= 2, 1 <= d <= BEAGLE_MAX_VARS. inputs_on_device: 0 = host pointers, 1 = device.
+ * Every value must be finite with |v| <= 1e30, and y must not be constant, else
+ * BEAGLE_ERR_DATASET. The library computes the target mean and sum of squares in fp64 and
+ * stores X, y and y - mean(y) in its own padded layout. The call returns once the data is
+ * on the device. *dataset_id receives a positive id.
+ */
+beagle_status beagle_upload_dataset(const float *X, const float *y, int64_t N, int32_t d,
+                                    int32_t inputs_on_device, void *stream,
+                                    int32_t *dataset_id);
+
+/* Release a dataset. Work already enqueued that uses it completes first (the call
+ * synchronises the device). BEAGLE_ERR_DATASET for an unknown id, BEAGLE_ERR_BUSY while a
+ * serving run still holds it. */
+beagle_status beagle_release_dataset(int32_t dataset_id);
+
+/* N, d, mean of y and sum_i (y_i - mean)^2 of a resident dataset (any pointer may be NULL). */
+beagle_status beagle_dataset_info(int32_t dataset_id, int64_t *N, int32_t *d, double *ybar,
+                                  double *syy);
+
+/*
+ * Host-side structural check of a population in the wire format (Section 3.2): every token
+ * finds its operands, the stack never holds more than max_depth values, variables exist,
+ * exactly one value remains, and 1 <= length <= BEAGLE_MAX_LENGTH. All pointers are host
+ * pointers. Returns BEAGLE_ERR_PROGRAM and the index of the first bad program in
+ * *first_bad (if not NULL), else BEAGLE_OK and -1.
+ */
+beagle_status beagle_validate_programs(const uint8_t *programs, const int64_t *offsets,
+                                       const int32_t *lengths, int64_t P, int32_t d,
+                                       int32_t max_depth, int64_t *first_bad);
+
+/*
+ * Score a population against a resident dataset (Section 2.4). All array pointers are
+ * device pointers:
+ *   programs  concatenated tokens; program p is programs[offsets[p] .. offsets[p]+lengths[p])
+ *   offsets   [P] int64, lengths [P] int32
+ *   consts    token-aligned fp32: consts[offsets[p] + j] is read when token j is CONST
+ *   fitness_out [P] beagle_fitness, written by the call
+ * precision is BEAGLE_FP32_COMPENSATED or BEAGLE_FP64. Programs are not checked on the
+ * host; a program that fails the structural check (or is deeper than BEAGLE_MAX_DEPTH or
+ * longer than BEAGLE_MAX_LENGTH) gets BEAGLE_FLAG_MALFORMED instead of a fitness.
+ * Asynchronous on stream; the call uses stream-ordered scratch memory that it frees itself.
+ * Results are deterministic: the same program and dataset give the same bits in any
+ * population and any batch.
+ */
+beagle_status beagle_score(const uint8_t *programs, const int64_t *offsets,
+                           const int32_t *lengths, const float *consts, int64_t P,
+                           int32_t dataset_id, beagle_fitness *fitness_out,
+                           int32_t precision, void *stream);
+
+/*
+ * Same as beagle_score with HOST arrays (pinned memory gives the fastest copies): copies the
+ * inputs to the device, scores, copies the fitness back and synchronises the stream before
+ * returning. consts_len is the number of floats in consts (the total token count).
+ */
+beagle_status beagle_score_host(const uint8_t *programs, const int64_t *offsets,
+                                const int32_t *lengths, const float *consts, int64_t P,
+                                int64_t n_tokens, int32_t dataset_id,
+                                beagle_fitness *fitness_out, int32_t precision, void *stream);
+
+/*
+ * Measurement support (not part of scoring).
+ * beagle_measure_op_rates: throughput of each operator on the current device, in operator
+ * evaluations per second, written to rates[opcode] for the ten arithmetic opcodes (other
+ * entries 0). Each evaluation includes the validity check the scoring kernels do; eight
+ * independent chains per thread at full occupancy, so the figure is what straight-line
+ * compiled code reaches. Synchronous; runs about seconds_hint seconds. n_rates >= 11.
+ * beagle_kernel_timing: enable (1) or disable (0) CUDA-event timing around every scoring
+ * kernel launch. beagle_kernel_time: synchronises on the recorded events, returns the summed
+ * kernel time (ms) and the number of launches since the previous query, and clears them.
+ */
+beagle_status beagle_measure_op_rates(double *rates, int32_t n_rates, double seconds_hint,
+                                      void *stream);
+beagle_status beagle_kernel_timing(int32_t enable);
+beagle_status beagle_kernel_time(double *total_ms, int64_t *launches);
+
+/* Message of the calling thread's most recent failure ("" if none). */
+const char *beagle_last_error(void);
+
+/* Library version, major * 10000 + minor * 100 + patch. */
+int32_t beagle_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BEAGLE_H */

@@ -1,0 +1,251 @@
+"""Thin Python binding of libbeagle.so (include/beagle.h), same names as the C ABI.
+
+Only argument marshalling happens here: pointers of torch CUDA tensors (or numpy arrays for
+host calls), sizes and the current torch stream are passed through ctypes. Every step of
+scoring runs in the library's CUDA kernels. There is no CPU fallback: if the library has not
+been built, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import numpy as np
+
+from . import build as _build
+
+OK = 0
+ERRORS = {-1: "BEAGLE_ERR_ARG", -2: "BEAGLE_ERR_PROGRAM", -3: "BEAGLE_ERR_DATASET",
+          -4: "BEAGLE_ERR_OOM", -5: "BEAGLE_ERR_CUDA", -6: "BEAGLE_ERR_TIMEOUT",
+          -7: "BEAGLE_ERR_BUSY", -8: "BEAGLE_ERR_LIMIT"}
+FP32_COMPENSATED, FP64 = 0, 1
+FLAG_INVALID, FLAG_DEGENERATE, FLAG_MALFORMED, FLAG_TIMEOUT = 1, 2, 4, 8
+MAX_VARS, MAX_DEPTH, MAX_LENGTH = 16, 16, 256
+
+# beagle_fitness: {double mse; double one_minus_r2; uint32 flags; uint32 reserved}
+FITNESS_DTYPE = np.dtype([("mse", "<f8"), ("one_minus_r2", "<f8"), ("flags", "<u4"),
+                          ("reserved", "<u4")])
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
+                      "include", "beagle.h")
+
+
+class BeagleError(RuntimeError):
+    def __init__(self, code: int, message: str):
+        super().__init__(f"{ERRORS.get(code, code)}: {message}")
+        self.code = code
+
+
+_lib = None
+_vp, _i32, _i64, _u8p = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_void_p
+
+_SIGNATURES = {
+    "beagle_upload_dataset": ([_vp, _vp, _i64, _i32, _i32, _vp, _vp], _i32),
+    "beagle_release_dataset": ([_i32], _i32),
+    "beagle_dataset_info": ([_i32, _vp, _vp, _vp, _vp], _i32),
+    "beagle_validate_programs": ([_vp, _vp, _vp, _i64, _i32, _i32, _vp], _i32),
+    "beagle_score": ([_vp, _vp, _vp, _vp, _i64, _i32, _vp, _i32, _vp], _i32),
+    "beagle_score_host": ([_vp, _vp, _vp, _vp, _i64, _i64, _i32, _vp, _i32, _vp], _i32),
+    "beagle_measure_op_rates": ([_vp, _i32, ctypes.c_double, _vp], _i32),
+    "beagle_kernel_timing": ([_i32], _i32),
+    "beagle_kernel_time": ([_vp, _vp], _i32),
+    "beagle_last_error": ([], ctypes.c_char_p),
+    "beagle_version": ([], _i32),
+}
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """The loaded library. Raises if it has not been built (no fallback exists)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(_build.LIB):
+            raise RuntimeError(f"{_build.LIB} is missing: build it first "
+                               "(python -m paper_2607_06731_gb300.build)")
+        L = ctypes.CDLL(_build.LIB)
+        for name, (args, res) in _SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = L
+    return _lib
+
+
+def header_functions() -> list[str]:
+    """Names of the functions include/beagle.h declares."""
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(beagle_[a-z_0-9]+)\s*\(", text)))
+
+
+def last_error() -> str:
+    return lib().beagle_last_error().decode()
+
+
+def version() -> int:
+    return int(lib().beagle_version())
+
+
+def check(rc: int):
+    if rc != OK:
+        raise BeagleError(rc, last_error())
+
+
+def _stream_handle(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if isinstance(t, np.ndarray):
+        return t.ctypes.data
+    return t.data_ptr()
+
+
+# ----------------------------------------------------------------------------- datasets
+class Dataset:
+    """A dataset resident on the current device (beagle_upload_dataset)."""
+
+    def __init__(self, X, y, stream=None):
+        import torch
+        on_device = isinstance(X, torch.Tensor) and X.is_cuda
+        if on_device:
+            X = X.detach().to(torch.float32).contiguous()
+            y = y.detach().to(torch.float32).contiguous()
+        else:
+            X = np.ascontiguousarray(X, np.float32)
+            y = np.ascontiguousarray(y, np.float32)
+        if X.ndim == 1:
+            X = X.reshape(1, -1)
+        d, N = int(X.shape[0]), int(X.shape[1])
+        if int(y.shape[0]) != N:
+            raise ValueError("y must have N entries")
+        out = ctypes.c_int32()
+        check(lib().beagle_upload_dataset(_ptr(X), _ptr(y), N, d, int(on_device),
+                                          _stream_handle(stream) if on_device else None,
+                                          ctypes.byref(out)))
+        self.id = int(out.value)
+        self.N, self.d = N, d
+        yb, syy = ctypes.c_double(), ctypes.c_double()
+        check(lib().beagle_dataset_info(self.id, None, None, ctypes.byref(yb), ctypes.byref(syy)))
+        self.ybar, self.syy = yb.value, syy.value
+
+    def release(self):
+        if self.id:
+            check(lib().beagle_release_dataset(self.id))
+            self.id = 0
+
+
+def upload_dataset(X, y, stream=None) -> Dataset:
+    return Dataset(X, y, stream)
+
+
+def release_dataset(ds: Dataset):
+    ds.release()
+
+
+# ----------------------------------------------------------------------------- programs
+def validate_programs(ops, offsets, lengths, d: int, max_depth: int = MAX_DEPTH):
+    """Host structural check; returns -1 if all programs are valid, else the first bad index."""
+    ops = np.ascontiguousarray(ops, np.uint8)
+    offsets = np.ascontiguousarray(offsets, np.int64)
+    lengths = np.ascontiguousarray(lengths, np.int32)
+    first = ctypes.c_int64(-1)
+    rc = lib().beagle_validate_programs(_ptr(ops), _ptr(offsets), _ptr(lengths), len(lengths),
+                                        d, max_depth, ctypes.byref(first))
+    if rc not in (OK, -2):
+        check(rc)
+    return int(first.value)
+
+
+class DevicePrograms:
+    """A population copied to the device in the wire format (torch tensors)."""
+
+    def __init__(self, progs, device="cuda"):
+        import torch
+        self.ops = torch.from_numpy(np.ascontiguousarray(progs.ops, np.uint8)).to(device)
+        self.offsets = torch.from_numpy(np.ascontiguousarray(progs.offsets, np.int64)).to(device)
+        self.lengths = torch.from_numpy(np.ascontiguousarray(progs.lengths, np.int32)).to(device)
+        self.consts = torch.from_numpy(np.ascontiguousarray(progs.consts, np.float32)).to(device)
+        self.P = int(progs.lengths.shape[0])
+        self.tokens = int(progs.ops.shape[0])
+
+
+def _precision(p) -> int:
+    if p in (FP32_COMPENSATED, "fp32c", "fp32"):
+        return FP32_COMPENSATED
+    if p in (FP64, "fp64"):
+        return FP64
+    raise ValueError(p)
+
+
+def score(programs, offsets, lengths, consts, dataset: Dataset, out=None,
+          precision="fp32c", stream=None):
+    """beagle_score on device tensors. Returns (and fills) a [P, 3] float64 CUDA tensor whose
+    rows are the 24-byte beagle_fitness records (see unpack_fitness)."""
+    import torch
+    P = int(lengths.shape[0])
+    if out is None:
+        out = torch.empty((P, 3), dtype=torch.float64, device=lengths.device)
+    check(lib().beagle_score(_ptr(programs), _ptr(offsets), _ptr(lengths), _ptr(consts), P,
+                             dataset.id, _ptr(out), _precision(precision),
+                             _stream_handle(stream)))
+    return out
+
+
+def score_programs(dp: DevicePrograms, dataset: Dataset, out=None, precision="fp32c",
+                   stream=None):
+    return score(dp.ops, dp.offsets, dp.lengths, dp.consts, dataset, out, precision, stream)
+
+
+def score_host(progs, dataset: Dataset, out=None, precision="fp32c", stream=None):
+    """beagle_score_host: host arrays in, host fitness records out (numpy structured array)."""
+    ops = np.ascontiguousarray(progs.ops, np.uint8)
+    offs = np.ascontiguousarray(progs.offsets, np.int64)
+    lens = np.ascontiguousarray(progs.lengths, np.int32)
+    cs = np.ascontiguousarray(progs.consts, np.float32)
+    P = len(lens)
+    if out is None:
+        out = np.zeros(P, FITNESS_DTYPE)
+    check(lib().beagle_score_host(_ptr(ops), _ptr(offs), _ptr(lens), _ptr(cs), P, len(ops),
+                                  dataset.id, _ptr(out), _precision(precision),
+                                  _stream_handle(stream)))
+    return out
+
+
+def unpack_fitness(out):
+    """(mse, one_minus_r2, flags) numpy arrays from a [P, 3] tensor or a structured array."""
+    if isinstance(out, np.ndarray) and out.dtype == FITNESS_DTYPE:
+        return out["mse"].copy(), out["one_minus_r2"].copy(), out["flags"].copy()
+    a = out.detach().cpu().numpy()
+    rec = np.ascontiguousarray(a).view(FITNESS_DTYPE).reshape(-1)
+    return rec["mse"].copy(), rec["one_minus_r2"].copy(), rec["flags"].copy()
+
+
+# ----------------------------------------------------------------------------- measurement
+def measure_op_rates(seconds_hint: float = 1.0, stream=None) -> dict:
+    """Operator evaluations per second on the current device, keyed by opcode."""
+    rates = (ctypes.c_double * 16)()
+    check(lib().beagle_measure_op_rates(rates, 16, seconds_hint, _stream_handle(stream)))
+    return {i: float(rates[i]) for i in range(16) if rates[i] > 0}
+
+
+def kernel_timing(enable: bool):
+    check(lib().beagle_kernel_timing(1 if enable else 0))
+
+
+def kernel_time():
+    """(total ms, launches) of the scoring kernels timed since the previous call."""
+    ms, n = ctypes.c_double(), ctypes.c_int64()
+    check(lib().beagle_kernel_time(ctypes.byref(ms), ctypes.byref(n)))
+    return ms.value, int(n.value)

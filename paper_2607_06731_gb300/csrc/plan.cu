@@ -1,0 +1,164 @@
+// Launch planning: tile size, work-item size, scratch layout and the enqueue of one
+// persistent scoring launch (plus finalize) per batch of up to kMaxJobs jobs.
+#include <algorithm>
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+#include "kernels.h"
+#include "registry.h"
+
+namespace beagle {
+
+namespace {
+
+struct Planned {
+    JobDev dev;
+    const CUtensorMap *map;
+    size_t part_bytes;
+};
+
+size_t up256(size_t x) { return (x + 255) / 256 * 256; }
+
+// Keep freed stream-ordered scratch in the device's default pool instead of returning it to
+// the driver at every synchronisation, so repeated calls do not remap memory.
+void keep_pool_memory(int dev) {
+    static std::mutex mu;
+    static std::vector<int> done;
+    std::lock_guard<std::mutex> lk(mu);
+    if (std::find(done.begin(), done.end(), dev) != done.end()) return;
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+        uint64_t keep = UINT64_MAX;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    }
+    done.push_back(dev);
+}
+
+template <int MAXJ>
+beagle_status enqueue(const std::vector<Planned> &jobs, size_t b, size_t e, int precision,
+                      int tile, int group, int grid, int xbuf_floats, cudaStream_t s) {
+    LaunchParams<MAXJ> prm;
+    std::memset(&prm, 0, sizeof prm);
+    size_t scratch = 256;
+    for (size_t i = b; i < e; ++i) scratch += up256(jobs[i].part_bytes);
+    char *base = nullptr;
+    cudaError_t err = cudaMallocAsync(reinterpret_cast<void **>(&base), scratch, s);
+    if (err != cudaSuccess)
+        return fail(BEAGLE_ERR_OOM, "scratch of %zu bytes: %s", scratch, cudaGetErrorString(err));
+    err = cudaMemsetAsync(base, 0, 256, s);
+    if (err != cudaSuccess) {
+        cudaFreeAsync(base, s);
+        return cuda_fail(err, "scratch memset");
+    }
+    prm.counter = reinterpret_cast<unsigned int *>(base);
+    prm.error = reinterpret_cast<unsigned int *>(base + 128);
+    char *cur = base + 256;
+    int64_t items = 0;
+    int nj = 0;
+    for (size_t i = b; i < e; ++i, ++nj) {
+        prm.maps[nj] = *jobs[i].map;
+        prm.jobs[nj] = jobs[i].dev;
+        prm.jobs[nj].partials = reinterpret_cast<uint32_t *>(cur);
+        cur += up256(jobs[i].part_bytes);
+        prm.jobs[nj].groups = static_cast<int32_t>((jobs[i].dev.P + group - 1) / group);
+        prm.jobs[nj].item0 = items;
+        items += static_cast<int64_t>(prm.jobs[nj].groups) * prm.jobs[nj].tiles;
+    }
+    prm.njobs = nj;
+    prm.total_items = items;
+    prm.tile = tile;
+    prm.group = group;
+    prm.xbuf_floats = xbuf_floats;
+    cudaError_t le;
+    if constexpr (MAXJ == 1) le = launch_score(prm, precision, grid, s);
+    else le = launch_score_batch(prm, precision, grid, s);
+    cudaFreeAsync(base, s);
+    if (le != cudaSuccess) return cuda_fail(le, "scoring launch");
+    return BEAGLE_OK;
+}
+
+}  // namespace
+
+beagle_status score_jobs(const JobRequest *reqs, int n, int precision, cudaStream_t s,
+                         const Tune *tune) {
+    if (n < 0 || (n > 0 && !reqs)) return fail(BEAGLE_ERR_ARG, "bad job list");
+    if (precision != BEAGLE_FP32_COMPENSATED && precision != BEAGLE_FP64)
+        return fail(BEAGLE_ERR_ARG, "unknown precision %d", precision);
+    int dev = 0;
+    cudaGetDevice(&dev);
+    keep_pool_memory(dev);
+    std::vector<std::shared_ptr<Dataset>> keep;
+    std::vector<Planned> jobs;
+    int max_rows = 1;
+    int64_t work = 0;
+    for (int i = 0; i < n; ++i) {
+        const JobRequest &r = reqs[i];
+        if (r.P < 0) return fail(BEAGLE_ERR_ARG, "job %d: negative P", i);
+        if (r.P > (int64_t(1) << 31) - 1) return fail(BEAGLE_ERR_LIMIT, "job %d: P >= 2^31", i);
+        auto ds = find_dataset(r.dataset_id);
+        if (!ds) return fail(BEAGLE_ERR_DATASET, "job %d: unknown dataset %d", i, r.dataset_id);
+        if (ds->device != dev)
+            return fail(BEAGLE_ERR_DATASET, "job %d: dataset %d lives on device %d, current is %d",
+                        i, r.dataset_id, ds->device, dev);
+        if (r.P == 0) continue;
+        if (!r.programs || !r.offsets || !r.lengths || !r.consts || !r.out)
+            return fail(BEAGLE_ERR_ARG, "job %d: null pointer argument", i);
+        Planned pj;
+        std::memset(&pj, 0, sizeof pj);
+        pj.dev.ops = r.programs;
+        pj.dev.offs = r.offsets;
+        pj.dev.lens = r.lengths;
+        pj.dev.consts = r.consts;
+        pj.dev.out = r.out;
+        pj.dev.order = r.order;
+        pj.dev.P = r.P;
+        pj.dev.N = ds->N;
+        pj.dev.d = ds->d;
+        pj.dev.rows = ds->rows;
+        pj.dev.ybar = ds->ybar;
+        pj.dev.syy = ds->syy;
+        pj.map = &ds->map;
+        max_rows = std::max(max_rows, ds->rows);
+        keep.push_back(ds);
+        jobs.push_back(pj);
+    }
+    if (jobs.empty()) return BEAGLE_OK;
+
+    // Tile: 1024 cases when two staged tiles of every job's rows fit, else 512. The FP64
+    // path keeps 512 (its per-warp output buffers hold doubles).
+    int tile = (precision == BEAGLE_FP64 || max_rows > 12) ? 512 : 1024;
+    if (tune && tune->tile) {
+        if (tune->tile != 512 && tune->tile != 1024)
+            return fail(BEAGLE_ERR_ARG, "tile must be 512 or 1024");
+        tile = tune->tile;
+    }
+    const int xbuf_floats = max_rows * tile;
+    int grid = (tune && tune->grid) ? tune->grid : sm_count();
+    size_t smem = smem_bytes(precision, xbuf_floats, tile);
+    if (smem > 227 * 1024)
+        return fail(BEAGLE_ERR_LIMIT, "shared memory plan of %zu bytes exceeds 227 KB", smem);
+    const int which = tile == 512 ? 0 : 1;
+    for (size_t i = 0; i < jobs.size(); ++i) {
+        JobDev &J = jobs[i].dev;
+        J.tiles = static_cast<int32_t>((J.N + tile - 1) / tile);
+        J.tile_sy = keep[i]->tile_sy[which];
+        jobs[i].part_bytes = static_cast<size_t>(kNumFields) * J.tiles * J.P * sizeof(uint32_t);
+        work += J.P * J.tiles;
+    }
+    // Programs per work item: about 32 items per CTA, at least 8 and at most 256 programs.
+    int group = static_cast<int>(std::min<int64_t>(256, std::max<int64_t>(8, work / (32LL * grid))));
+    if (tune && tune->group) group = tune->group;
+
+    if (jobs.size() == 1)
+        return enqueue<1>(jobs, 0, 1, precision, tile, group, grid, xbuf_floats, s);
+    for (size_t b = 0; b < jobs.size(); b += kMaxJobs) {
+        const size_t e = std::min(jobs.size(), b + kMaxJobs);
+        beagle_status st = enqueue<kMaxJobs>(jobs, b, e, precision, tile, group, grid,
+                                             xbuf_floats, s);
+        if (st != BEAGLE_OK) return st;
+    }
+    return BEAGLE_OK;
+}
+
+}  // namespace beagle

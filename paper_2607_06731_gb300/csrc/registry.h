@@ -1,0 +1,56 @@
+// Host-side state shared by the C-ABI translation units.
+#pragma once
+
+#include <memory>
+
+#include "common.cuh"
+
+namespace beagle {
+
+constexpr int kTileSizes[2] = {512, 1024};   // cases per tile the kernels support
+
+// A resident dataset: rows x_0..x_{d-1}, y, y - ybar, each padded to npad floats.
+struct Dataset {
+    int32_t id = 0;
+    int device = 0;
+    int64_t N = 0;
+    int32_t d = 0, rows = 0;
+    int64_t npad = 0;
+    float *data = nullptr;                    // device [rows][npad]
+    double *tile_sy[2] = {nullptr, nullptr};  // device, per tile size (512, 1024)
+    CUtensorMap map;                          // box: 256 cases x rows
+    double ybar = 0.0, syy = 0.0;
+    int holds = 0;                            // serving runs that keep it resident
+    ~Dataset();
+};
+
+std::shared_ptr<Dataset> find_dataset(int32_t id);
+
+// One (population, dataset) pair to score.
+struct JobRequest {
+    const uint8_t *programs;
+    const int64_t *offsets;
+    const int32_t *lengths;
+    const float *consts;
+    int64_t P;
+    int32_t dataset_id;
+    beagle_fitness *out;
+    const int32_t *order;   // optional device permutation of [0, P), may be null
+};
+
+// Launch-shape overrides (0 = choose automatically).
+struct Tune {
+    int group = 0;   // programs per work item
+    int tile = 0;    // cases per tile (512 or 1024)
+    int grid = 0;    // CTAs
+};
+
+// Enqueue scoring of n jobs on stream s (one persistent launch per 64 jobs).
+beagle_status score_jobs(const JobRequest *reqs, int n, int precision, cudaStream_t s,
+                         const Tune *tune);
+
+beagle_status fail(beagle_status code, const char *fmt, ...);
+beagle_status cuda_fail(cudaError_t e, const char *what);
+int sm_count();
+
+}  // namespace beagle

@@ -1,0 +1,369 @@
+// Persistent scoring kernel and the fp64 finalize kernel (see score.cuh for the design).
+#include <cstdio>
+
+#include "score.cuh"
+#include "kernels.h"
+
+namespace beagle {
+
+// Shared-memory layout of one CTA (dynamic):
+//   [0, 64)        mbarriers: full[2], empty[2]
+//   [64, 128)      slot descriptors (2 x Slot)
+//   [128, ...)     X stage buffers: 2 x xbuf_floats fp32 (TMA destinations, 128-byte aligned)
+//   ...            per-warp output buffers: NW x tile x T
+//   ...            per-warp packed programs: NW x (kMaxLen + 2) x uint2
+struct Slot {
+    int job;        // -1: no more work
+    int tile;
+    int group;
+    int next;       // next program of the item (shared-memory counter)
+};
+
+template <typename T, int K, int NW>
+struct SmemLayout {
+    static __host__ __device__ size_t xbuf_off() { return 128; }
+    static __host__ __device__ size_t fbuf_off(int xbuf_floats) {
+        return xbuf_off() + 2ull * xbuf_floats * sizeof(float);
+    }
+    static __host__ __device__ size_t pbuf_off(int xbuf_floats, int tile) {
+        return fbuf_off(xbuf_floats) + static_cast<size_t>(NW) * tile * sizeof(T);
+    }
+    static __host__ __device__ size_t total(int xbuf_floats, int tile) {
+        return pbuf_off(xbuf_floats, tile) + static_cast<size_t>(NW) * (kMaxLen + 2) * sizeof(uint2);
+    }
+};
+
+template <typename T, int K, int D>
+__device__ void process_program(const JobDev &J, int64_t p, int t, int tile, const float *xs,
+                                uint2 *pbuf, T *fbuf, int lane) {
+    using Sum = typename SumOf<T>::type;
+    constexpr int CH = 32 * K;
+    const int64_t off = J.offs[p];
+    const int L = J.lens[p];
+    const Packed pk = pack_program<T, D>(J.ops + off, J.consts + off, L, J.d, pbuf, lane);
+
+    const int64_t P = J.P;
+    const int tiles = J.tiles;
+    uint32_t *part = J.partials;
+    auto field = [&](int f) -> uint32_t * {
+        return part + (static_cast<int64_t>(f) * tiles + t) * P + p;
+    };
+    if (pk.malformed) {
+        if (lane == 0) *field(kTileFlags) = TF_MALFORMED;
+        return;
+    }
+    const int64_t tstart = static_cast<int64_t>(t) * tile;
+    const int nval = static_cast<int>(min(static_cast<int64_t>(tile), J.N - tstart));
+    const int rows = J.rows;
+
+    bool anybad = pk.const_bad;
+    for (int c0 = 0; c0 < nval; c0 += CH) {
+        const float *xrow = xs + (c0 / kBox) * rows * kBox + (c0 % kBox) + lane * K;
+        T f[K];
+        bool bad[K];
+        run_program<T, K, D>(pbuf, pk.n, xrow, f, bad);
+        T *dst = fbuf + c0 + lane * K;
+#pragma unroll
+        for (int j = 0; j < K; ++j) {
+            dst[j] = f[j];
+            if (bad[j] && c0 + lane * K + j < nval) anybad = true;
+        }
+    }
+    anybad = __any_sync(kFull, anybad);
+    __syncwarp();
+    if (anybad) {
+        if (lane == 0) *field(kTileFlags) = TF_INVALID;
+        return;
+    }
+
+    // Two passes over the tile's outputs: the tile mean first, then sums centred on it.
+    const float *yrow = xs + J.d * kBox;          // target row
+    const float *ycrow = xs + (J.d + 1) * kBox;   // centred-target row
+    auto at = [&](const float *row, int i) { return row[(i / kBox) * rows * kBox + (i % kBox)]; };
+    const T f0 = fbuf[0];
+    Sum sf, se;
+    bool nonconst = false;
+    for (int i = lane; i < nval; i += 32) {
+        const T fi = fbuf[i];
+        const T e = fi - static_cast<T>(at(yrow, i));
+        se.add(e * e);
+        sf.add(fi);
+        nonconst |= (fi != f0);
+    }
+    nonconst = __any_sync(kFull, nonconst);
+    sf.warp_allreduce();
+    se.warp_allreduce();
+    T m;
+    if constexpr (sizeof(T) == 4) m = nonconst ? (sf.s + sf.c) / static_cast<float>(nval) : f0;
+    else m = nonconst ? sf.s / static_cast<double>(nval) : f0;
+    Sum sd, sdd, sdy;
+    if (nonconst) {
+        for (int i = lane; i < nval; i += 32) {
+            const T dv = fbuf[i] - m;
+            sd.add(dv);
+            sdd.add(dv * dv);
+            sdy.add(dv * static_cast<T>(at(ycrow, i)));
+        }
+        sd.warp_allreduce();
+        sdd.warp_allreduce();
+        sdy.warp_allreduce();
+    }
+    if (lane == 0) {
+        uint32_t w[kNumFields];
+        if constexpr (sizeof(T) == 4) {
+            w[kMean] = __float_as_uint(m);
+            w[kMean64] = 0u;
+        } else {
+            const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(m));
+            w[kMean] = static_cast<uint32_t>(b);
+            w[kMean64] = static_cast<uint32_t>(b >> 32);
+        }
+        put_pair(w + kSe2, se);
+        put_pair(w + kSd, sd);
+        put_pair(w + kSdd, sdd);
+        put_pair(w + kSdy, sdy);
+        w[kTileFlags] = nonconst ? TF_NONCONST : 0u;
+#pragma unroll
+        for (int f = 0; f < kNumFields; ++f) *field(f) = w[f];
+    }
+    __syncwarp();
+}
+
+template <int MAXJ>
+__device__ __forceinline__ int find_job(const LaunchParams<MAXJ> &prm, int64_t item) {
+    int j = 0;
+    while (j + 1 < prm.njobs && item >= prm.jobs[j + 1].item0) ++j;
+    return j;
+}
+
+template <typename T, int K, int D, int NW, int MAXJ>
+__global__ void __launch_bounds__((NW + 1) * 32, 1)
+score_kernel(const __grid_constant__ LaunchParams<MAXJ> prm) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    using Lay = SmemLayout<T, K, NW>;
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem);
+    uint64_t *empty = full + 2;
+    Slot *slots = reinterpret_cast<Slot *>(smem + 64);
+    float *xbuf = reinterpret_cast<float *>(smem + Lay::xbuf_off());
+    T *fbuf_all = reinterpret_cast<T *>(smem + Lay::fbuf_off(prm.xbuf_floats));
+    uint2 *pbuf_all = reinterpret_cast<uint2 *>(smem + Lay::pbuf_off(prm.xbuf_floats, prm.tile));
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int tile = prm.tile;
+    if (threadIdx.x == 0) {
+        mbar_init(&full[0], 1);
+        mbar_init(&full[1], 1);
+        mbar_init(&empty[0], NW);
+        mbar_init(&empty[1], NW);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+
+    if (warp == NW) {
+        // Producer: claim items, stage their X/y tile with TMA, publish the slot.
+        if (lane == 0) {
+            int k = 0;
+            for (;; ++k) {
+                const int b = k & 1;
+                if (k >= 2 && !mbar_wait(&empty[b], ((k >> 1) - 1) & 1)) {
+                    atomicOr(prm.error, kErrTimeoutEmpty);
+                    break;
+                }
+                const int64_t item = static_cast<int64_t>(atomicAdd(prm.counter, 1u));
+                Slot &s = slots[b];
+                if (item >= prm.total_items) {
+                    s.job = -1;
+                    mbar_arrive(&full[b]);
+                    break;
+                }
+                const int j = find_job(prm, item);
+                const JobDev &J = prm.jobs[j];
+                const int64_t local = item - J.item0;
+                const int t = static_cast<int>(local / J.groups);
+                const int g = static_cast<int>(local % J.groups);
+                s.job = j;
+                s.tile = t;
+                s.group = g;
+                s.next = 0;
+                const int boxes = tile / kBox;
+                const uint32_t bytes = static_cast<uint32_t>(boxes * J.rows * kBox * sizeof(float));
+                mbar_arrive_expect_tx(&full[b], bytes);
+                float *dst = xbuf + static_cast<size_t>(b) * prm.xbuf_floats;
+                for (int q = 0; q < boxes; ++q)
+                    tma_load_2d(dst + q * J.rows * kBox, &prm.maps[j], t * tile + q * kBox, 0,
+                                &full[b]);
+            }
+            // Let the copies this thread issued land before the CTA can exit: consumers
+            // wait on every published slot, so only a timed-out run needs this wait.
+            if (k >= 1) (void)mbar_wait(&full[(k - 1) & 1], ((k - 1) >> 1) & 1);
+        }
+        return;
+    }
+
+    // Consumers
+    T *fbuf = fbuf_all + static_cast<size_t>(warp) * tile;
+    uint2 *pbuf = pbuf_all + static_cast<size_t>(warp) * (kMaxLen + 2);
+    for (int k = 0;; ++k) {
+        const int b = k & 1;
+        if (!mbar_wait(&full[b], (k >> 1) & 1)) {
+            if (lane == 0) atomicOr(prm.error, kErrTimeoutFull);
+            break;
+        }
+        const volatile Slot *vs = &slots[b];
+        Slot s;
+        s.job = vs->job;
+        s.tile = vs->tile;
+        s.group = vs->group;
+        if (s.job < 0) break;
+        const JobDev &J = prm.jobs[s.job];
+        const float *xs = xbuf + static_cast<size_t>(b) * prm.xbuf_floats;
+        const int64_t p0 = static_cast<int64_t>(s.group) * prm.group;
+        const int64_t p1 = min(J.P, p0 + prm.group);
+        for (;;) {
+            int idx = 0;
+            if (lane == 0) idx = atomicAdd(&slots[b].next, 1);
+            idx = __shfl_sync(kFull, idx, 0);
+            const int64_t q = p0 + idx;
+            if (q >= p1) break;
+            const int64_t p = J.order ? static_cast<int64_t>(J.order[q]) : q;
+            process_program<T, K, D>(J, p, s.tile, tile, xs, pbuf, fbuf, lane);
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[b]);
+    }
+}
+
+// Finalize: merge each program's tiles in a fixed order in fp64 (Chan et al.'s pairwise
+// update of centred sums), then MSE and 1 - r^2 (Eq. 1, squared).
+template <bool FP64>
+__device__ __forceinline__ double word_pair(const uint32_t *w0, const uint32_t *w1) {
+    if constexpr (FP64) {
+        return __longlong_as_double(static_cast<long long>(
+            (static_cast<unsigned long long>(*w1) << 32) | *w0));
+    } else {
+        return static_cast<double>(__uint_as_float(*w0)) +
+               static_cast<double>(__uint_as_float(*w1));
+    }
+}
+
+template <bool FP64, int MAXJ>
+__global__ void finalize_kernel(const __grid_constant__ LaunchParams<MAXJ> prm) {
+    const int jn = blockIdx.y;
+    if (jn >= prm.njobs) return;
+    const JobDev &J = prm.jobs[jn];
+    const int64_t p = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (p >= J.P) return;
+    const int T = J.tiles;
+    const int64_t P = J.P;
+    auto W = [&](int f, int t) { return J.partials + (static_cast<int64_t>(f) * T + t) * P + p; };
+    beagle_fitness r;
+    r.reserved = 0u;
+    const double inf = __longlong_as_double(0x7ff0000000000000ll);
+    uint32_t flags = 0u;
+    if (*prm.error != 0u) {
+        r.mse = r.one_minus_r2 = __longlong_as_double(0x7ff8000000000000ll);
+        r.flags = BEAGLE_FLAG_TIMEOUT;
+        J.out[p] = r;
+        return;
+    }
+    bool nonconst = false, mdiff = false;
+    double sse = 0.0, sumf = 0.0, m0 = 0.0;
+    for (int t = 0; t < T; ++t) {
+        const uint32_t tf = *W(kTileFlags, t);
+        if (tf & TF_MALFORMED) flags |= BEAGLE_FLAG_MALFORMED;
+        if (tf & TF_INVALID) flags |= BEAGLE_FLAG_INVALID;
+    }
+    if (flags) {
+        r.mse = r.one_minus_r2 = inf;
+        r.flags = flags;
+        J.out[p] = r;
+        return;
+    }
+    for (int t = 0; t < T; ++t) {
+        const double n = static_cast<double>(min(static_cast<int64_t>(prm.tile),
+                                                 J.N - static_cast<int64_t>(t) * prm.tile));
+        const double m = FP64 ? word_pair<true>(W(kMean, t), W(kMean64, t))
+                              : static_cast<double>(__uint_as_float(*W(kMean, t)));
+        sse += word_pair<FP64>(W(kSe2, t), W(kSe2 + 1, t));
+        sumf += n * m + word_pair<FP64>(W(kSd, t), W(kSd + 1, t));
+        nonconst |= (*W(kTileFlags, t) & TF_NONCONST) != 0u;
+        if (t == 0) m0 = m;
+        else mdiff |= (m != m0);
+    }
+    const double N = static_cast<double>(J.N);
+    r.mse = sse / N;
+    if (!nonconst && !mdiff) {
+        r.one_minus_r2 = 1.0;
+        r.flags = BEAGLE_FLAG_DEGENERATE;
+        J.out[p] = r;
+        return;
+    }
+    const double fbar = sumf / N;
+    double sff = 0.0, sfy = 0.0;
+    for (int t = 0; t < T; ++t) {
+        const double n = static_cast<double>(min(static_cast<int64_t>(prm.tile),
+                                                 J.N - static_cast<int64_t>(t) * prm.tile));
+        const double m = FP64 ? word_pair<true>(W(kMean, t), W(kMean64, t))
+                              : static_cast<double>(__uint_as_float(*W(kMean, t)));
+        const double dm = m - fbar;
+        const double sd = word_pair<FP64>(W(kSd, t), W(kSd + 1, t));
+        sff += word_pair<FP64>(W(kSdd, t), W(kSdd + 1, t)) + 2.0 * dm * sd + n * dm * dm;
+        sfy += word_pair<FP64>(W(kSdy, t), W(kSdy + 1, t)) + dm * J.tile_sy[t];
+    }
+    if (!(sff > 0.0)) {
+        r.one_minus_r2 = 1.0;
+        r.flags = BEAGLE_FLAG_DEGENERATE;
+    } else {
+        const double rr = sfy / sqrt(sff * J.syy);
+        r.one_minus_r2 = 1.0 - rr * rr;
+        r.flags = 0u;
+    }
+    J.out[p] = r;
+}
+
+// --------------------------------------------------------------------------- launchers
+template <typename T, int K, int D, int NW, int MAXJ>
+static cudaError_t launch_impl(const LaunchParams<MAXJ> &prm, int grid, cudaStream_t stream) {
+    using Lay = SmemLayout<T, K, NW>;
+    const size_t smem = Lay::total(prm.xbuf_floats, prm.tile);
+    auto kern = score_kernel<T, K, D, NW, MAXJ>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(smem));
+    if (e != cudaSuccess) return e;
+    void *tok = nullptr;
+    const bool timed = timing_enabled();
+    if (timed) timing_begin(stream, &tok);
+    kern<<<grid, (NW + 1) * 32, smem, stream>>>(prm);
+    e = cudaGetLastError();
+    if (timed) timing_end(stream, tok);
+    if (e != cudaSuccess) return e;
+    int64_t maxP = 0;
+    for (int j = 0; j < prm.njobs; ++j) maxP = maxP > prm.jobs[j].P ? maxP : prm.jobs[j].P;
+    if (maxP > 0) {
+        dim3 fg(static_cast<unsigned>((maxP + 255) / 256), static_cast<unsigned>(prm.njobs));
+        if (sizeof(T) == 8) finalize_kernel<true, MAXJ><<<fg, 256, 0, stream>>>(prm);
+        else finalize_kernel<false, MAXJ><<<fg, 256, 0, stream>>>(prm);
+        e = cudaGetLastError();
+    }
+    return e;
+}
+
+size_t smem_bytes(int precision, int xbuf_floats, int tile) {
+    if (precision == BEAGLE_FP64) return SmemLayout<double, kCasesFp64, kWarpsFp64>::total(xbuf_floats, tile);
+    return SmemLayout<float, kCasesFp32, kWarpsFp32>::total(xbuf_floats, tile);
+}
+
+cudaError_t launch_score(const LaunchParams<1> &prm, int precision, int grid, cudaStream_t s) {
+    if (precision == BEAGLE_FP64)
+        return launch_impl<double, kCasesFp64, kMaxDepth, kWarpsFp64, 1>(prm, grid, s);
+    return launch_impl<float, kCasesFp32, kMaxDepth, kWarpsFp32, 1>(prm, grid, s);
+}
+
+cudaError_t launch_score_batch(const LaunchParams<kMaxJobs> &prm, int precision, int grid,
+                               cudaStream_t s) {
+    if (precision == BEAGLE_FP64)
+        return launch_impl<double, kCasesFp64, kMaxDepth, kWarpsFp64, kMaxJobs>(prm, grid, s);
+    return launch_impl<float, kCasesFp32, kMaxDepth, kWarpsFp32, kMaxJobs>(prm, grid, s);
+}
+
+}  // namespace beagle

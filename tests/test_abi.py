@@ -1,0 +1,85 @@
+"""C-ABI checks that need no GPU: the library loads, exports every function the header
+declares, agrees with the generator and the oracle on the wire format, and its host-side
+structural check agrees with the oracle's."""
+from __future__ import annotations
+
+import ctypes
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2607_06731_gb300 import beagle, synth as S
+from paper_2607_06731_gb300 import build as B
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    B.build()
+    yield
+
+
+def test_library_exports_every_header_function():
+    names = beagle.header_functions()
+    assert "beagle_score" in names and "beagle_upload_dataset" in names
+    L = ctypes.CDLL(B.LIB)
+    for n in names:
+        assert hasattr(L, n), n
+
+
+def test_version_and_error_without_gpu():
+    assert beagle.version() == 100
+    assert isinstance(beagle.last_error(), str)
+
+
+def _header_defines():
+    out = {}
+    for m in re.finditer(r"#define\s+(BEAGLE_\w+)\s+(-?\d+)u?", open(beagle.HEADER).read()):
+        out[m.group(1)] = int(m.group(2))
+    return out
+
+
+def test_wire_format_agrees_across_header_generator_and_oracle():
+    h = _header_defines()
+    names = ["CONST", "ADD", "SUB", "MUL", "PDIV", "SIN", "COS", "EXP", "PLOG", "PSQRT",
+             "SQUARE", "DUP", "SWAP", "DEL", "LOAD0"]
+    for n in names:
+        assert h[f"BEAGLE_OP_{n}"] == getattr(S, n), n
+    src = open(oracle._SRC).read()
+    for n in names:
+        m = re.search(rf"\bT_{n}\s*=\s*(\d+)", src)
+        assert m and int(m.group(1)) == getattr(S, n), n
+    assert h["BEAGLE_MAX_VARS"] == S.MAX_VARS
+    assert h["BEAGLE_FLAG_INVALID"] == oracle.F_INVALID
+    assert h["BEAGLE_FLAG_DEGENERATE"] == oracle.F_DEGENERATE
+    assert h["BEAGLE_FLAG_MALFORMED"] == oracle.F_MALFORMED
+    assert beagle.FITNESS_DTYPE.itemsize == 24
+
+
+def test_host_validation_agrees_with_oracle():
+    rng = np.random.default_rng(5)
+    ok = S.gen_programs(rng, 300, 1, 60, 3)
+    assert beagle.validate_programs(ok.ops, ok.offsets, ok.lengths, 3) == -1
+    alphabet = np.array([S.CONST, S.ADD, S.SUB, S.SIN, S.DUP, S.SWAP, S.DEL, S.LOAD0,
+                         S.LOAD0 + 2, S.LOAD0 + 3, 14, 99], np.uint8)
+    for _ in range(400):
+        L = int(rng.integers(1, 9))
+        ops = rng.choice(alphabet, L).astype(np.uint8)
+        want = oracle.check_program(ops, 3, 16)
+        got = beagle.validate_programs(ops, np.zeros(1, np.int64), np.array([L], np.int32), 3)
+        assert (got == -1) == (want == 0), (ops, want, got)
+    # depth limit and length limit
+    deep = np.array([S.CONST] * 17 + [S.ADD] * 16, np.uint8)
+    assert beagle.validate_programs(deep, [0], [len(deep)], 1) == 0
+    assert beagle.validate_programs(deep, [0], [len(deep)], 1, max_depth=32) == -1
+    long = np.array([S.CONST] + [S.SIN] * 256, np.uint8)
+    assert beagle.validate_programs(long, [0], [257], 1, max_depth=32) == 0
+
+
+def test_score_rejects_unknown_dataset_without_touching_a_gpu():
+    rc = beagle.lib().beagle_score(None, None, None, None, 0, 12345, None, 0, None)
+    assert rc == -3
+    assert "unknown dataset" in beagle.last_error()
+    rc = beagle.lib().beagle_score(None, None, None, None, 0, 12345, None, 7, None)
+    assert rc == -1

@@ -1,0 +1,288 @@
+"""Parity of the CUDA scoring path (through the C ABI) with the oracle, on the GPU."""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2607_06731_gb300 import beagle, synth as S
+from tests import parity
+from tests.gcl_text import paper_genomes
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import __graft_entry__
+    __graft_entry__.build()
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    yield
+
+
+def run_gpu(progs, X, y, precision="fp32c", ds=None):
+    own = ds is None
+    if own:
+        ds = beagle.Dataset(X, y)
+    dp = beagle.DevicePrograms(progs)
+    out = beagle.score_programs(dp, ds, precision=precision)
+    torch.cuda.synchronize()
+    r = beagle.unpack_fitness(out)
+    if own:
+        ds.release()
+    return r
+
+
+def oracles(progs, X, y):
+    return (oracle.score_programs(progs, X, y, "fp32"),
+            oracle.score_programs(progs, X, y, "fp64"))
+
+
+def full_check(progs, X, y, min_robust=0.8, fp64=True):
+    o32, o64 = oracles(progs, X, y)
+    g32 = run_gpu(progs, X, y, "fp32c")
+    frac = parity.check_fp32(g32, o32, o64, min_robust=min_robust)
+    if fp64:
+        g64 = run_gpu(progs, X, y, "fp64")
+        parity.check_fp64(g64, o32, o64)
+    return frac
+
+
+def test_c1_plain_scoring_full_size():
+    """P = 1024 programs of length 8-32 on N = 1024 cases, d = 2 (one tile)."""
+    pr = S.make_c1()
+    frac = full_check(pr.programs, pr.X, pr.y)
+    print(f"c1 robust fraction {frac:.4f}")
+
+
+def test_c2_distribution_small_population():
+    pr = S.make_c2(P=3000)
+    full_check(pr.programs, pr.X, pr.y)
+
+
+@pytest.mark.parametrize("N,d", [(2500, 10), (700, 16), (2, 1), (1025, 3), (3000, 13),
+                                 (1024, 12), (4096, 5)])
+def test_multi_tile_and_ragged_tail(N, d):
+    rng = np.random.default_rng(N * 31 + d)
+    X = rng.uniform(-3, 3, size=(d, N)).astype(np.float32)
+    y = (np.sin(X[0]) * 2 + X[-1] + rng.normal(0, 0.1, N)).astype(np.float32)
+    progs = S.gen_programs(rng, 500, 4, 64, d)
+    full_check(progs, X, y)
+
+
+def test_c2_full_population_sampled():
+    """The bench workload (P = 100,000, L 16-128, d = 5, N = 1024) in the launch bench.py
+    times; a seeded sample of programs is checked against the oracle one by one."""
+    pr = S.make_c2()
+    g32 = run_gpu(pr.programs, pr.X, pr.y, "fp32c")
+    idx = np.random.default_rng(0).choice(pr.programs.P, 1500, replace=False)
+    sub = pr.programs.subset(idx)
+    o32, o64 = oracles(sub, pr.X, pr.y)
+    parity.check_fp32(tuple(a[idx] for a in g32), o32, o64)
+
+
+def test_c3_full_size_sampled():
+    """P = 50,000 programs on N = 1,000,000 cases (977 tiles): every program scored on the
+    GPU, a sample checked against the oracle at the full case count. The FP64 path is
+    checked on a subset of the population."""
+    pr = S.make_c3()
+    ds = beagle.Dataset(pr.X, pr.y)
+    g32 = run_gpu(pr.programs, pr.X, pr.y, "fp32c", ds=ds)
+    idx = np.random.default_rng(1).choice(pr.programs.P, 48, replace=False)
+    sub = pr.programs.subset(idx)
+    o32, o64 = oracles(sub, pr.X, pr.y)
+    parity.check_fp32(tuple(a[idx] for a in g32), o32, o64, min_robust=0.6)
+    g64 = run_gpu(sub, pr.X, pr.y, "fp64", ds=ds)
+    parity.check_fp64(g64, o32, o64)
+    ds.release()
+
+
+def _quadratic(n=1024, seed=3):
+    rng = np.random.default_rng(seed)
+    a = rng.uniform(0.2, 3.0, n) * rng.choice([-1, 1], n)
+    b = rng.uniform(-6, 6, n)
+    c = rng.uniform(-3, 3, n)
+    X = np.stack([a, b, c]).astype(np.float32)
+    A, B, C = (X[i].astype(np.float64) for i in range(3))
+    X = X[:, B * B - 4 * A * C >= 0]
+    A, B, C = (X[i].astype(np.float64) for i in range(3))
+    y = ((-B + np.sqrt(B * B - 4 * A * C)) / (2 * A)).astype(np.float32)
+    return X, y
+
+
+def test_paper_genomes_on_gpu():
+    """Section 3.3's genomes (DUP, DEL, DIV by self, SQUARE) solve the quadratic."""
+    X, y = _quadratic()
+    progs = S.from_token_lists([t for _, t in paper_genomes().values()])
+    o32, o64 = oracles(progs, X, y)
+    g32 = run_gpu(progs, X, y, "fp32c")
+    g64 = run_gpu(progs, X, y, "fp64")
+    parity.check_fp32(g32, o32, o64, min_robust=0.0)
+    parity.check_fp64(g64, o32, o64)
+    assert np.all(g64[1] < 1e-12) and np.all(g32[1] < 1e-6)
+    assert np.all(g32[2] == 0)
+
+
+def _stack_ops_programs(rng, P, d):
+    """Random programs that also use DUP, SWAP and DEL."""
+    progs = []
+    for _ in range(P):
+        L = int(rng.integers(3, 40))
+        toks, depth = [], 0
+        for t in range(L):
+            r = L - t
+            choices = []
+            if depth + 1 <= 16 and depth <= r - 1:
+                choices += ["leaf", "leaf", "dup"] if depth >= 1 else ["leaf"]
+            if depth >= 1 and depth - 1 <= r - 1:
+                choices += ["un"]
+            if depth >= 2 and depth - 2 <= r - 1:
+                choices += ["bin", "bin", "swap", "del"]
+            if depth >= 1 and depth - 1 <= r - 1 and depth >= 2:
+                choices += ["swap"]
+            k = choices[int(rng.integers(len(choices)))]
+            if k == "dup" and depth + 1 > 16:
+                k = "un"
+            if k == "leaf":
+                if rng.random() < 0.5:
+                    toks.append((S.LOAD0 + int(rng.integers(d)), 0.0))
+                else:
+                    toks.append((S.CONST, float(np.float32(rng.uniform(-2, 2)))))
+                depth += 1
+            elif k == "dup":
+                toks.append((S.DUP, 0.0)); depth += 1
+            elif k == "un":
+                toks.append((int(rng.choice(S.UNARY)), 0.0))
+            elif k == "swap":
+                toks.append((S.SWAP, 0.0))
+            elif k == "del":
+                toks.append((S.DEL, 0.0)); depth -= 1
+            else:
+                toks.append((int(rng.choice(S.BINARY)), 0.0)); depth -= 1
+        if depth == 1 and oracle.check_program([t[0] for t in toks], d, 16) == 0:
+            progs.append(toks)
+    return S.from_token_lists(progs)
+
+
+def test_dup_swap_del():
+    rng = np.random.default_rng(17)
+    d = 3
+    progs = _stack_ops_programs(rng, 800, d)
+    assert progs.P > 300
+    X = rng.uniform(-3, 3, size=(d, 1500)).astype(np.float32)
+    y = (X[0] * X[1] + rng.normal(0, 0.1, 1500)).astype(np.float32)
+    full_check(progs, X, y, min_robust=0.7)
+
+
+def test_malformed_programs_are_flagged():
+    C, L0 = S.CONST, S.LOAD0
+    good = [(C, 1.5), (L0, 0), (S.ADD, 0)]
+    bad = [
+        [(S.ADD, 0)],                                   # underflow
+        [(C, 1.0), (C, 2.0)],                           # two values left
+        [(L0 + 3, 0)],                                  # x3 with d = 2
+        [(20, 0)],                                      # unknown opcode
+        [(C, 1.0)] * 17 + [(S.ADD, 0)] * 16,            # 17 values > BEAGLE_MAX_DEPTH
+        [(C, 1.0)] + [(S.SIN, 0)] * 256,                # 257 tokens > BEAGLE_MAX_LENGTH
+    ]
+    ok_deep = [(C, 1.0)] * 16 + [(S.ADD, 0)] * 15       # exactly 16 deep
+    ok_long = [(L0, 0)] + [(S.SIN, 0)] * 255            # exactly 256 tokens
+    progs = S.from_token_lists([good] + bad + [ok_deep, ok_long])
+    X = np.random.default_rng(0).uniform(-1, 1, size=(2, 300)).astype(np.float32)
+    y = X[0].copy()
+    for prec in ("fp32c", "fp64"):
+        m, r, f = run_gpu(progs, X, y, prec)
+        assert f[0] == 0
+        assert np.all(f[1:1 + len(bad)] == beagle.FLAG_MALFORMED), f
+        assert np.all(np.isinf(m[1:1 + len(bad)]))
+        assert f[-2] & beagle.FLAG_MALFORMED == 0 and f[-1] & beagle.FLAG_MALFORMED == 0
+    o32, o64 = oracles(S.from_token_lists([good, ok_deep, ok_long]), X, y)
+    g32 = run_gpu(S.from_token_lists([good, ok_deep, ok_long]), X, y, "fp32c")
+    parity.check_fp32(g32, o32, o64, min_robust=0.0)
+
+
+def test_invalid_values_and_constants():
+    C = S.CONST
+    progs = S.from_token_lists([
+        [(C, float("inf"))],                            # non-finite constant
+        [(C, 100.0), (S.EXP, 0)],                       # e^100 > 1e30
+        [(C, 1.0), (C, 1e16), (C, 1e15), (S.MUL, 0), (S.PDIV, 0)],   # hidden 1e31
+        [(C, 2.0 ** 49), (S.SQUARE, 0)],                # 2^98 < 1e30: valid
+        [(S.LOAD0, 0), (C, 50.0), (S.MUL, 0), (S.EXP, 0)],   # overflow on some cases
+    ])
+    X = np.linspace(-1, 1, 1000, dtype=np.float32).reshape(1, -1)
+    y = X[0] * 2
+    for prec in ("fp32c", "fp64"):
+        m, r, f = run_gpu(progs, X, y, prec)
+        assert list(f & 1) == [1, 1, 1, 0, 1], (prec, f)
+        assert np.isinf(m[0]) and np.isinf(r[0])
+
+
+def test_constant_outputs_are_degenerate_across_tiles():
+    progs = S.from_token_lists([[(S.CONST, 1.25)],
+                                [(S.LOAD0, 0), (S.LOAD0, 0), (S.SUB, 0)],
+                                [(S.LOAD0, 0), (S.SIN, 0)]])
+    X = np.random.default_rng(2).uniform(-2, 2, size=(1, 3000)).astype(np.float32)
+    y = (X[0] ** 2).astype(np.float32)
+    for prec in ("fp32c", "fp64"):
+        m, r, f = run_gpu(progs, X, y, prec)
+        assert list(f) == [2, 2, 0] and r[0] == 1.0 and r[1] == 1.0
+        want = np.mean((1.25 - y.astype(np.float64)) ** 2)
+        assert abs(m[0] - want) <= 1e-6 * want
+
+
+def test_empty_population():
+    X = np.ones((1, 4), np.float32) * np.arange(4, dtype=np.float32)
+    ds = beagle.Dataset(X, X[0])
+    e = torch.empty(0, dtype=torch.uint8, device="cuda")
+    out = beagle.score(e, e.long(), e.int(), e.float(), ds)
+    torch.cuda.synchronize()
+    assert out.shape == (0, 3)
+    ds.release()
+
+
+def test_same_bits_alone_and_in_a_mix():
+    """Fixed-order reductions: a program's fitness does not depend on its neighbours."""
+    pr = S.make_c2(P=4000, N=3000)
+    ds = beagle.Dataset(pr.X, pr.y)
+    full = run_gpu(pr.programs, pr.X, pr.y, "fp32c", ds=ds)
+    idx = np.random.default_rng(4).choice(pr.programs.P, 300, replace=False)
+    alone = run_gpu(pr.programs.subset(idx), pr.X, pr.y, "fp32c", ds=ds)
+    for a, b in zip(full, alone):
+        assert np.array_equal(a[idx], b, equal_nan=True)
+    again = run_gpu(pr.programs, pr.X, pr.y, "fp32c", ds=ds)
+    for a, b in zip(full, again):
+        assert np.array_equal(a, b, equal_nan=True)
+    ds.release()
+
+
+def test_score_host_matches_device_call():
+    pr = S.make_c1(P=500)
+    ds = beagle.Dataset(pr.X, pr.y)
+    dev = run_gpu(pr.programs, pr.X, pr.y, "fp32c", ds=ds)
+    host = beagle.unpack_fitness(beagle.score_host(pr.programs, ds, precision="fp32c"))
+    for a, b in zip(dev, host):
+        assert np.array_equal(a, b, equal_nan=True)
+    ds.release()
+
+
+def test_dataset_upload_from_device_and_rejections():
+    rng = np.random.default_rng(0)
+    X = rng.uniform(-1, 1, size=(3, 100)).astype(np.float32)
+    y = X[0] + X[1]
+    a = beagle.Dataset(X, y)
+    b = beagle.Dataset(torch.from_numpy(X).cuda(), torch.from_numpy(y).cuda())
+    assert abs(a.ybar - b.ybar) == 0 and a.syy == b.syy
+    pr = S.gen_programs(rng, 50, 4, 20, 3)
+    ra = run_gpu(pr, X, y, ds=a)
+    rb = run_gpu(pr, X, y, ds=b)
+    assert np.array_equal(ra[0], rb[0], equal_nan=True)
+    a.release(), b.release()
+    with pytest.raises(beagle.BeagleError):
+        beagle.Dataset(X, np.ones(100, np.float32))          # constant y
+    Xn = X.copy(); Xn[1, 5] = np.nan
+    with pytest.raises(beagle.BeagleError):
+        beagle.Dataset(Xn, y)
+    with pytest.raises(beagle.BeagleError):
+        beagle.Dataset(np.ones((17, 10), np.float32), np.arange(10, dtype=np.float32))
