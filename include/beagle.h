@@ -145,6 +145,18 @@ beagle_status beagle_score(const uint8_t *programs, const int64_t *offsets,
                            int32_t precision, void *stream);
 
 /*
+ * Run each program on every case and keep the outputs (the paper's ExecuteGenome utility,
+ * Section 3.8): same arguments and results as beagle_score, plus outputs, a device array of
+ * P x N values (row p holds program p's output on every case), fp32 for
+ * BEAGLE_FP32_COMPENSATED and fp64 for BEAGLE_FP64. Outputs of malformed programs are not
+ * written. Asynchronous on stream.
+ */
+beagle_status beagle_eval(const uint8_t *programs, const int64_t *offsets,
+                          const int32_t *lengths, const float *consts, int64_t P,
+                          int32_t dataset_id, void *outputs, beagle_fitness *fitness_out,
+                          int32_t precision, void *stream);
+
+/*
  * Same as beagle_score with HOST arrays (pinned memory gives the fastest copies): copies the
  * inputs to the device, scores, copies the fitness back and synchronises the stream before
  * returning. consts_len is the number of floats in consts (the total token count).

@@ -23,7 +23,13 @@ _SRC = os.path.join(_HERE, "oracle.c")
 _LIB = os.path.join(_HERE, "liboracle.so")
 
 FP64, FP32 = 0, 1
-F_INVALID, F_DEGENERATE, F_MALFORMED, F_NEAR = 1, 2, 4, 256
+F_INVALID, F_DEGENERATE, F_MALFORMED, F_NEAR, F_AMBIG = 1, 2, 4, 256, 512
+
+# Documented maximum errors (units in the last place) of CUDA's math functions, used as the
+# device's per-operator accuracy in the error bounds: sinf/cosf/expf 2, logf 1;
+# sin/cos/exp/log (double) 2, 2, 1, 1. Indexed by opcode.
+DEV_ULPS_FP32 = {5: 2.0, 6: 2.0, 7: 2.0, 8: 1.0}
+DEV_ULPS_FP64 = {5: 2.0, 6: 2.0, 7: 1.0, 8: 1.0}
 STACK = 32
 CHECK_ERRORS = {0: "ok", 1: "underflow", 2: "overflow", 3: "final depth", 4: "opcode",
                 5: "variable", 6: "empty"}
@@ -58,6 +64,13 @@ def lib():
                                    ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, P, P, P]
         L.oracle_score.restype = ctypes.c_int
         L.oracle_threads.restype = ctypes.c_int
+        L.oracle_eval_bound.argtypes = [P, P, ctypes.c_int32, P, ctypes.c_int64,
+                                        ctypes.c_int32, ctypes.c_int32, P, P, P]
+        L.oracle_eval_bound.restype = ctypes.c_uint32
+        L.oracle_score_bound.argtypes = [P, P, P, P, ctypes.c_int64, P, P, ctypes.c_int64,
+                                         ctypes.c_int32, ctypes.c_int32, P, ctypes.c_int32,
+                                         P, P, P, P, P]
+        L.oracle_score_bound.restype = ctypes.c_int
         _lib = L
     return _lib
 
@@ -131,3 +144,50 @@ def score(ops, offsets, lengths, consts, X, y, mode="fp64", nthreads: int = 0):
 def score_programs(progs, X, y, mode="fp64", nthreads: int = 0):
     """Same as ``score`` for any object with ops/offsets/lengths/consts attributes."""
     return score(progs.ops, progs.offsets, progs.lengths, progs.consts, X, y, mode, nthreads)
+
+
+def _ulps(mode, dev_ulps):
+    if dev_ulps is None:
+        dev_ulps = DEV_ULPS_FP32 if _mode(mode) == FP32 else DEV_ULPS_FP64
+    a = np.zeros(64, np.float64)
+    for k, v in dev_ulps.items():
+        a[k] = v
+    return a
+
+
+def eval_bound(ops, consts, X, mode="fp32", dev_ulps=None):
+    """Per-case outputs, per-case error bounds and flags (running error analysis)."""
+    ops = np.ascontiguousarray(ops, np.uint8)
+    consts = np.ascontiguousarray(consts, np.float32)
+    X = np.ascontiguousarray(X, np.float32)
+    if X.ndim == 1:
+        X = X[None, :]
+    d, N = X.shape
+    f = np.zeros(N, np.float64)
+    dl = np.zeros(N, np.float64)
+    u = _ulps(mode, dev_ulps)
+    fl = lib().oracle_eval_bound(_p(ops), _p(consts), len(ops), _p(X), N, d, _mode(mode),
+                                 _p(u), _p(f), _p(dl))
+    return f, dl, int(fl)
+
+
+def score_bound(progs, X, y, mode="fp32", dev_ulps=None, nthreads: int = 0):
+    """(mse, one_minus_r2, flags, mse_bound, one_minus_r2_bound) for a population."""
+    ops = np.ascontiguousarray(progs.ops, np.uint8)
+    offsets = np.ascontiguousarray(progs.offsets, np.int64)
+    lengths = np.ascontiguousarray(progs.lengths, np.int32)
+    consts = np.ascontiguousarray(progs.consts, np.float32)
+    X = np.ascontiguousarray(X, np.float32)
+    if X.ndim == 1:
+        X = X[None, :]
+    y = np.ascontiguousarray(y, np.float32)
+    d, N = X.shape
+    P = len(lengths)
+    out = [np.zeros(P, np.float64), np.zeros(P, np.float64), np.zeros(P, np.uint32),
+           np.zeros(P, np.float64), np.zeros(P, np.float64)]
+    u = _ulps(mode, dev_ulps)
+    rc = lib().oracle_score_bound(_p(ops), _p(offsets), _p(lengths), _p(consts), P, _p(X),
+                                  _p(y), N, d, _mode(mode), _p(u), nthreads, *map(_p, out))
+    if rc != 0:
+        raise ValueError("oracle_score_bound rejected its arguments")
+    return tuple(out)

@@ -48,6 +48,7 @@ enum { ORACLE_FP64 = 0, ORACLE_FP32 = 1 };
 #define OF_DEGENERATE 2u    /* the program's output is the same on every case: r undefined */
 #define OF_MALFORMED  4u    /* the token list is not a valid program */
 #define OF_NEAR     256u    /* diagnostic: a value came within 1e-5 (relative) of a threshold */
+#define OF_AMBIG    512u    /* error bound: a threshold or validity decision lies inside it */
 
 #define ORACLE_STACK 32     /* StackSize (Section 3.2) */
 
@@ -274,4 +275,204 @@ int oracle_threads(void) {
 #else
     return 1;
 #endif
+}
+
+
+/* ------------------------------------------------------------------------------------
+ * Running error analysis (first order, after Wilkinson): alongside each value v of the
+ * oracle's evaluation in the given mode, carry a bound D on |v_dev - v|, where v_dev is the
+ * value a device computes with the same operation order and precision but with sin, cos,
+ * exp and log accurate only to dev_ulps[op] units in the last place (a library's documented
+ * maximum error). + - * / sqrt are correctly rounded on both sides, so they add error only
+ * when their inputs already differ. The oracle's own transcendental results are within
+ * own_ulps (0.5 in FP32 mode: double results rounded to fp32; 1 in FP64 mode).
+ * A decision (protection threshold, validity limit) whose operand lies within D of the
+ * threshold is ambiguous and sets OF_AMBIG.
+ * ---------------------------------------------------------------------------------- */
+static double ulp_at(double r, int mode) {
+    double a = fabs(r);
+    if (!isfinite(a)) return INFINITY;
+    if (mode == ORACLE_FP32) {
+        float f = (float)a;
+        return (double)nextafterf(f, INFINITY) - (double)f;
+    }
+    return nextafter(a, INFINITY) - a;
+}
+
+static double run_case_bound(const uint8_t *ops, const float *cs, int32_t L, const float *x,
+                             int64_t ldx, int mode, const double *dev_ulps, double *delta,
+                             int *bad, int *ambig) {
+    double st[ORACLE_STACK + 1], dt[ORACLE_STACK + 1];
+    int sp = 0;
+    const double big = big_limit(mode), tiny = tiny_limit(mode);
+    const double own = mode == ORACLE_FP32 ? 0.5 : 1.0;
+    for (int32_t j = 0; j < L; ++j) {
+        int op = ops[j];
+        double v, d;
+        if (op == T_CONST || op >= T_LOAD0) {
+            v = op == T_CONST ? (double)cs[j] : (double)x[(int64_t)(op - T_LOAD0) * ldx];
+            st[sp] = v; dt[sp] = 0.0; ++sp;
+            if (!(fabs(v) <= big)) *bad = 1;
+            continue;
+        } else if (op == T_DUP) {
+            st[sp] = st[sp - 1]; dt[sp] = dt[sp - 1]; ++sp;
+            continue;
+        } else if (op == T_SWAP) {
+            double t = st[sp - 1]; st[sp - 1] = st[sp - 2]; st[sp - 2] = t;
+            t = dt[sp - 1]; dt[sp - 1] = dt[sp - 2]; dt[sp - 2] = t;
+            continue;
+        } else if (op == T_DEL) {
+            --sp;
+            continue;
+        } else if (op <= T_PDIV) {
+            double b = st[--sp], db = dt[sp];
+            double a = st[--sp], da = dt[sp];
+            switch (op) {
+            case T_ADD: v = a + b; d = da + db; break;
+            case T_SUB: v = a - b; d = da + db; break;
+            case T_MUL: v = a * b; d = fabs(b) * da + fabs(a) * db + da * db; break;
+            default:
+                if (fabs(fabs(b) - tiny) <= db) *ambig = 1;
+                if (fabs(b) > tiny) {
+                    v = a / b;
+                    d = db > 0.0 ? (fabs(b) > db ? (da + fabs(v) * db) / (fabs(b) - db)
+                                                 : INFINITY)
+                                 : da / fabs(b);
+                } else {
+                    v = 1.0; d = 0.0;
+                }
+                break;
+            }
+            v = round_to(v, mode);
+            if (d > 0.0) d += ulp_at(v, mode);
+        } else {
+            double a = st[--sp], da = dt[sp];
+            double u = dev_ulps[op] + own;
+            switch (op) {
+            case T_SIN: v = sin(a); d = da + u * ulp_at(round_to(v, mode), mode); break;
+            case T_COS: v = cos(a); d = da + u * ulp_at(round_to(v, mode), mode); break;
+            case T_EXP:
+                v = exp(a);
+                d = fabs(v) * expm1(da) + u * ulp_at(round_to(v, mode), mode);
+                break;
+            case T_PLOG:
+                if (fabs(fabs(a) - tiny) <= da) *ambig = 1;
+                if (fabs(a) > tiny) {
+                    v = log(fabs(a));
+                    d = (fabs(a) > da ? da / (fabs(a) - da) : INFINITY) +
+                        u * ulp_at(round_to(v, mode), mode);
+                } else {
+                    v = 0.0; d = 0.0;
+                }
+                break;
+            case T_PSQRT:
+                v = sqrt(fabs(a));
+                d = da > 0.0 ? sqrt(fabs(a) + da) - sqrt(fmax(fabs(a) - da, 0.0)) : 0.0;
+                if (d > 0.0) d += ulp_at(round_to(v, mode), mode);
+                break;
+            default:   /* SQUARE */
+                v = a * a;
+                d = 2.0 * fabs(a) * da + da * da;
+                if (d > 0.0) d += ulp_at(round_to(v, mode), mode);
+                break;
+            }
+            v = round_to(v, mode);
+        }
+        if (!isfinite(d)) *ambig = 1;
+        if (fabs(v) <= big && fabs(v) + d > big) *ambig = 1;
+        if (!(fabs(v) <= big)) {
+            if (isfinite(fabs(v)) && fabs(v) - d <= big) *ambig = 1;
+            *bad = 1;
+        }
+        st[sp] = v; dt[sp] = d; ++sp;
+    }
+    *delta = dt[0];
+    return st[0];
+}
+
+/* Per-case values, error bounds and flags of one program (see run_case_bound). */
+uint32_t oracle_eval_bound(const uint8_t *ops, const float *cs, int32_t L, const float *X,
+                           int64_t N, int32_t d, int32_t mode, const double *dev_ulps,
+                           double *f, double *delta) {
+    if (oracle_check_program(ops, L, d, ORACLE_STACK) != OE_OK) return OF_MALFORMED;
+    uint32_t flags = 0;
+    for (int64_t i = 0; i < N; ++i) {
+        int bad = 0, ambig = 0;
+        f[i] = run_case_bound(ops, cs, L, X + i, N, mode, dev_ulps, &delta[i], &bad, &ambig);
+        if (bad) flags |= OF_INVALID;
+        if (ambig) flags |= OF_AMBIG;
+    }
+    return flags;
+}
+
+/*
+ * Bounds on the fitness a device may report, from the per-case bounds D_i:
+ *   |SSE_dev - SSE| <= sum (2 |e_i| D_i + D_i^2)
+ *   S_fy moves by at most A = sum D_i |y_i - ybar|, S_ff by at most
+ *   B = sum (2 |f_i - fbar| D_i + D_i^2); r^2 = S_fy^2 / (S_ff S_yy) then stays within the
+ *   interval given by the extreme corners.
+ * A program whose output is constant keeps it constant on the device (every case runs the
+ * same operations on the same values); its 1 - r^2 bound is 0.
+ */
+void oracle_fitness_bound(const double *f, const double *delta, const float *y, int64_t N,
+                          uint32_t flags, double *bmse, double *bomr2) {
+    if (flags & (OF_INVALID | OF_MALFORMED)) { *bmse = 0.0; *bomr2 = 0.0; return; }
+    nsum sy = {0, 0}, sf = {0, 0};
+    int constant = 1;
+    for (int64_t i = 0; i < N; ++i) {
+        nadd(&sy, (double)y[i]);
+        nadd(&sf, f[i]);
+        if (f[i] != f[0]) constant = 0;
+    }
+    const double ybar = nval(&sy) / (double)N, fbar = nval(&sf) / (double)N;
+    nsum be = {0, 0}, ba = {0, 0}, bb = {0, 0}, sff = {0, 0}, syy = {0, 0}, sfy = {0, 0};
+    for (int64_t i = 0; i < N; ++i) {
+        const double e = f[i] - (double)y[i], yc = (double)y[i] - ybar, fc = f[i] - fbar;
+        const double D = delta[i];
+        nadd(&be, 2.0 * fabs(e) * D + D * D);
+        nadd(&ba, D * fabs(yc));
+        nadd(&bb, 2.0 * fabs(fc) * D + D * D);
+        nadd(&sff, fc * fc);
+        nadd(&syy, yc * yc);
+        nadd(&sfy, fc * yc);
+    }
+    *bmse = nval(&be) / (double)N;
+    if (constant) { *bomr2 = 0.0; return; }
+    const double A = nval(&ba), B = nval(&bb), Sff = nval(&sff), Syy = nval(&syy);
+    const double Sfy = fabs(nval(&sfy));
+    if (!(Sff - B > 0.0)) { *bomr2 = INFINITY; return; }
+    const double r2 = Sfy * Sfy / (Sff * Syy);
+    const double hi = (Sfy + A) * (Sfy + A) / ((Sff - B) * Syy);
+    const double lo_n = Sfy > A ? (Sfy - A) : 0.0;
+    const double lo = lo_n * lo_n / ((Sff + B) * Syy);
+    *bomr2 = fmax(hi - r2, r2 - lo);
+}
+
+/* Population version: values, flags and fitness bounds (one parallel loop over programs). */
+int oracle_score_bound(const uint8_t *programs, const int64_t *offsets, const int32_t *lengths,
+                       const float *consts, int64_t P, const float *X, const float *y,
+                       int64_t N, int32_t d, int32_t mode, const double *dev_ulps,
+                       int32_t nthreads, double *mse, double *omr2, uint32_t *flags,
+                       double *bmse, double *bomr2) {
+    if (N <= 0 || P < 0) return -1;
+#ifdef _OPENMP
+    if (nthreads <= 0) nthreads = omp_get_max_threads();
+#pragma omp parallel num_threads(nthreads)
+#endif
+    {
+        double *f = (double *)malloc(sizeof(double) * (size_t)N);
+        double *dl = (double *)malloc(sizeof(double) * (size_t)N);
+#ifdef _OPENMP
+#pragma omp for schedule(dynamic, 4)
+#endif
+        for (int64_t p = 0; p < P; ++p) {
+            uint32_t fl = oracle_eval_bound(programs + offsets[p], consts + offsets[p],
+                                            lengths[p], X, N, d, mode, dev_ulps, f, dl);
+            oracle_aggregate(f, y, N, fl, &mse[p], &omr2[p], &flags[p]);
+            oracle_fitness_bound(f, dl, y, N, fl, &bmse[p], &bomr2[p]);
+        }
+        free(f);
+        free(dl);
+    }
+    return 0;
 }

@@ -46,6 +46,7 @@ _SIGNATURES = {
     "beagle_dataset_info": ([_i32, _vp, _vp, _vp, _vp], _i32),
     "beagle_validate_programs": ([_vp, _vp, _vp, _i64, _i32, _i32, _vp], _i32),
     "beagle_score": ([_vp, _vp, _vp, _vp, _i64, _i32, _vp, _i32, _vp], _i32),
+    "beagle_eval": ([_vp, _vp, _vp, _vp, _i64, _i32, _vp, _vp, _i32, _vp], _i32),
     "beagle_score_host": ([_vp, _vp, _vp, _vp, _i64, _i64, _i32, _vp, _i32, _vp], _i32),
     "beagle_measure_op_rates": ([_vp, _i32, ctypes.c_double, _vp], _i32),
     "beagle_kernel_timing": ([_i32], _i32),
@@ -201,6 +202,19 @@ def score(programs, offsets, lengths, consts, dataset: Dataset, out=None,
                              dataset.id, _ptr(out), _precision(precision),
                              _stream_handle(stream)))
     return out
+
+
+def eval_programs(dp: "DevicePrograms", dataset: "Dataset", precision="fp32c", stream=None):
+    """beagle_eval: per-case outputs [P, N] (float32 or float64 CUDA tensor) and fitness."""
+    import torch
+    prec = _precision(precision)
+    dt = torch.float64 if prec == FP64 else torch.float32
+    outputs = torch.full((dp.P, dataset.N), float("nan"), dtype=dt, device=dp.lengths.device)
+    fit = torch.empty((dp.P, 3), dtype=torch.float64, device=dp.lengths.device)
+    check(lib().beagle_eval(_ptr(dp.ops), _ptr(dp.offsets), _ptr(dp.lengths), _ptr(dp.consts),
+                            dp.P, dataset.id, _ptr(outputs), _ptr(fit), prec,
+                            _stream_handle(stream)))
+    return outputs, fit
 
 
 def score_programs(dp: DevicePrograms, dataset: Dataset, out=None, precision="fp32c",

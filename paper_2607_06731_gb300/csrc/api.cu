@@ -47,6 +47,8 @@ Dataset::~Dataset() {
     if (data) cudaFree(data);
     if (tile_sy[0]) cudaFree(tile_sy[0]);
     if (tile_sy[1]) cudaFree(tile_sy[1]);
+    if (tile_sy64[0]) cudaFree(tile_sy64[0]);
+    if (tile_sy64[1]) cudaFree(tile_sy64[1]);
 }
 
 // Neumaier-compensated fp64 accumulator.
@@ -153,15 +155,23 @@ beagle_status beagle_upload_dataset(const float *X, const float *y, int64_t N, i
     for (int which = 0; which < 2; ++which) {
         const int tile = kTileSizes[which];
         const int64_t T = (N + tile - 1) / tile;
-        std::vector<double> ts(static_cast<size_t>(T));
+        std::vector<double> ts(static_cast<size_t>(T)), ts64(static_cast<size_t>(T));
         for (int64_t t = 0; t < T; ++t) {
-            Acc a;
-            for (int64_t i = t * tile; i < std::min(N, (t + 1) * tile); ++i) a.add(yc[i]);
+            Acc a, a64;
+            for (int64_t i = t * tile; i < std::min(N, (t + 1) * tile); ++i) {
+                a.add(yc[i]);
+                a64.add(static_cast<double>(hy[i]) - ybar);
+            }
             ts[static_cast<size_t>(t)] = a.value();
+            ts64[static_cast<size_t>(t)] = a64.value();
         }
         cudaError_t e = cudaMalloc(&ds->tile_sy[which], ts.size() * sizeof(double));
         if (e == cudaSuccess)
             e = cudaMemcpy(ds->tile_sy[which], ts.data(), ts.size() * sizeof(double),
+                           cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMalloc(&ds->tile_sy64[which], ts64.size() * sizeof(double));
+        if (e == cudaSuccess)
+            e = cudaMemcpy(ds->tile_sy64[which], ts64.data(), ts64.size() * sizeof(double),
                            cudaMemcpyHostToDevice);
         if (e != cudaSuccess) return fail(BEAGLE_ERR_OOM, "dataset upload: %s", cudaGetErrorString(e));
     }
@@ -258,7 +268,18 @@ beagle_status beagle_score(const uint8_t *programs, const int64_t *offsets,
                            const int32_t *lengths, const float *consts, int64_t P,
                            int32_t dataset_id, beagle_fitness *fitness_out,
                            int32_t precision, void *stream) {
-    JobRequest req{programs, offsets, lengths, consts, P, dataset_id, fitness_out, nullptr};
+    JobRequest req{programs, offsets, lengths, consts, P, dataset_id, fitness_out, nullptr,
+                   nullptr};
+    return score_jobs(&req, 1, precision, static_cast<cudaStream_t>(stream), nullptr);
+}
+
+beagle_status beagle_eval(const uint8_t *programs, const int64_t *offsets,
+                          const int32_t *lengths, const float *consts, int64_t P,
+                          int32_t dataset_id, void *outputs, beagle_fitness *fitness_out,
+                          int32_t precision, void *stream) {
+    if (P > 0 && !outputs) return fail(BEAGLE_ERR_ARG, "outputs is null");
+    JobRequest req{programs, offsets, lengths, consts, P, dataset_id, fitness_out, nullptr,
+                   outputs};
     return score_jobs(&req, 1, precision, static_cast<cudaStream_t>(stream), nullptr);
 }
 

@@ -43,8 +43,9 @@ struct JobDev {
     const float *consts;
     beagle_fitness *out;
     uint32_t *partials;      // [kNumFields][tiles][P]
-    const double *tile_sy;   // [tiles] sum of (y - ybar) (stored fp32 values) per tile
+    const double *tile_sy;   // [tiles] per-tile sum of the centred targets the kernel uses
     const int32_t *order;    // optional [P] permutation (programs in processing order)
+    void *fout;              // optional [P][N] per-case outputs (float or double), else null
     int64_t P;
     int64_t N;
     int64_t item0;           // first global work item of this job

@@ -112,6 +112,7 @@ beagle_status score_jobs(const JobRequest *reqs, int n, int precision, cudaStrea
         pj.dev.consts = r.consts;
         pj.dev.out = r.out;
         pj.dev.order = r.order;
+        pj.dev.fout = r.fout;
         pj.dev.P = r.P;
         pj.dev.N = ds->N;
         pj.dev.d = ds->d;
@@ -142,7 +143,7 @@ beagle_status score_jobs(const JobRequest *reqs, int n, int precision, cudaStrea
     for (size_t i = 0; i < jobs.size(); ++i) {
         JobDev &J = jobs[i].dev;
         J.tiles = static_cast<int32_t>((J.N + tile - 1) / tile);
-        J.tile_sy = keep[i]->tile_sy[which];
+        J.tile_sy = precision == BEAGLE_FP64 ? keep[i]->tile_sy64[which] : keep[i]->tile_sy[which];
         jobs[i].part_bytes = static_cast<size_t>(kNumFields) * J.tiles * J.P * sizeof(uint32_t);
         work += J.P * J.tiles;
     }

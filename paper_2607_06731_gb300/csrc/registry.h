@@ -17,7 +17,9 @@ struct Dataset {
     int32_t d = 0, rows = 0;
     int64_t npad = 0;
     float *data = nullptr;                    // device [rows][npad]
-    double *tile_sy[2] = {nullptr, nullptr};  // device, per tile size (512, 1024)
+    double *tile_sy[2] = {nullptr, nullptr};    // device, per tile size (512, 1024): sums of
+                                                // the stored fp32 values of y - ybar
+    double *tile_sy64[2] = {nullptr, nullptr};  // same, of (double)y - ybar (FP64 path)
     CUtensorMap map;                          // box: 256 cases x rows
     double ybar = 0.0, syy = 0.0;
     int holds = 0;                            // serving runs that keep it resident
@@ -36,6 +38,7 @@ struct JobRequest {
     int32_t dataset_id;
     beagle_fitness *out;
     const int32_t *order;   // optional device permutation of [0, P), may be null
+    void *fout;             // optional device [P][N] per-case outputs, may be null
 };
 
 // Launch-shape overrides (0 = choose automatically).

@@ -71,6 +71,10 @@ __device__ void process_program(const JobDev &J, int64_t p, int t, int tile, con
     }
     anybad = __any_sync(kFull, anybad);
     __syncwarp();
+    if (J.fout) {   // per-case outputs requested (beagle_eval)
+        T *dst = static_cast<T *>(J.fout) + p * J.N + tstart;
+        for (int i = lane; i < nval; i += 32) dst[i] = fbuf[i];
+    }
     if (anybad) {
         if (lane == 0) *field(kTileFlags) = TF_INVALID;
         return;
@@ -127,7 +131,10 @@ __device__ void process_program(const JobDev &J, int64_t p, int t, int tile, con
             const T dv = (fi - m) * sd_scale;
             sd.add(dv);
             sdd.add(dv * dv);
-            sdy.add(dv * (static_cast<T>(at(ycrow, i)) * sy_scale));
+            // FP32: the stored fp32 y - ybar; FP64: y - ybar formed in fp64.
+            const T yc = sizeof(T) == 4 ? static_cast<T>(at(ycrow, i))
+                                        : static_cast<T>(at(yrow, i)) - static_cast<T>(J.ybar);
+            sdy.add(dv * (yc * sy_scale));
         }
     }
     se.warp_allreduce();

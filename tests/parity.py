@@ -2,21 +2,20 @@
 
 Random programs can be ill-conditioned (cancellation, exp chains, sin of huge arguments), so
 fp32 program arithmetic cannot match an fp64 evaluation within 1e-5 for every program. The
-gates therefore run the oracle twice, in FP64 and in FP32-ops mode (every op rounded to
-fp32), and call a program *robust* when
-  * both oracle runs agree on all flags and neither saw a value within 1e-5 of a threshold
-    (oracle NEAR bit),
-  * their fitnesses agree within 1e-6, and
-  * a first-order bound of the fitness change caused by the per-case output differences
-    delta_i = |f32_i - f64_i|, summed without cancellation, is below 1e-6 (relative):
-      SSE: 2 sum |e_i| delta_i;   r^2: r^2 (2 sum delta_i |yc_i| / |S_fy| + 2 sum |fc_i| delta_i / S_ff).
-    The GPU's fp32 transcendentals differ from the oracle's by a few ulp per op, so a program
-    whose outputs move less than 1e-6 under fp32 rounding moves well under 1e-5 on the GPU.
-  Gate A  GPU FP32  vs oracle FP32-ops  on robust programs, 1e-5 rel (1e-7 abs)
-  Gate B  GPU FP32  vs oracle FP64      on robust programs, 1e-5 rel (1e-7 abs)
-  Gate C  GPU FP64  vs oracle FP64      on robust programs, 1e-12 rel (1e-13 abs)
-Flags (INVALID, DEGENERATE, MALFORMED) must be equal on robust programs; off the robust set
-their mismatches are counted and bounded.
+oracle therefore also runs a first-order running error analysis (oracle.score_bound): next
+to its FP32-ops (or FP64) result it carries, per case, a bound on how far a device that
+computes the same operations with sin, cos, exp, log accurate to CUDA's documented ulp
+bounds can land from it, and turns those into bounds Bm, Br on the MSE and 1 - r^2. A
+program is AMBIGUOUS when some threshold or validity decision falls inside its bound.
+
+  Flags     exact on every non-ambiguous program.
+  Envelope  every non-ambiguous valid program: |g - o| <= tol_rel |o| + tol_abs + B.
+  Strict    programs with B <= 1e-6 |o| (+1e-9) whose FP32-ops and FP64 oracle results agree
+            within 1e-6 (the well-conditioned set):
+              gate A  GPU FP32 vs oracle FP32-ops, 1e-5 rel (1e-7 abs)
+              gate B  GPU FP32 vs oracle FP64,     1e-5 rel (1e-7 abs)
+            and, with the FP64 bound <= 1e-13,
+              gate C  GPU FP64 vs oracle FP64,     1e-12 rel (1e-13 abs)
 """
 from __future__ import annotations
 
@@ -29,93 +28,76 @@ TOL32 = (1e-5, 1e-7)
 TOL64 = (1e-12, 1e-13)
 
 
-def close(a, b, rel, abs_):
+def close(a, b, rel, abs_, extra=0.0):
     a = np.asarray(a, np.float64)
     b = np.asarray(b, np.float64)
     both_inf = np.isinf(a) & np.isinf(b) & (np.sign(a) == np.sign(b))
     with np.errstate(invalid="ignore"):
-        ok = np.abs(a - b) <= np.maximum(rel * np.abs(b), abs_)
+        ok = np.abs(a - b) <= np.maximum(rel * np.abs(b), abs_) + extra
     return ok | both_inf
 
 
-def _case_bound_ok(progs, X, y, p, rel):
-    ops, cs = progs.program(p)
-    f32, fl32 = oracle.eval_program(ops, cs, X, "fp32")
-    f64, fl64 = oracle.eval_program(ops, cs, X, "fp64")
-    if (fl32 | fl64) & (oracle.F_INVALID | oracle.F_MALFORMED):
-        return True                     # decided by the flags alone
-    yd = np.asarray(y, np.float64)
-    n = len(yd)
-    dlt = np.abs(f32 - f64)
-    e = f64 - yd
-    sse = float(e @ e)
-    if 2.0 * float(np.abs(e) @ dlt) > max(rel * sse, 1e-8 * n):
-        return False
-    yc = yd - yd.mean()
-    syy = float(yc @ yc)
-    fc = f64 - f64.mean()
-    sff = float(fc @ fc)
-    sfy = float(fc @ yc)
-    if sff == 0.0 or sfy == 0.0:
-        return True
-    r2 = sfy * sfy / (sff * syy)
-    br = r2 * (2.0 * float(dlt @ np.abs(yc)) / abs(sfy) + 2.0 * float(np.abs(fc) @ dlt) / sff)
-    return br <= max(rel * abs(1.0 - r2), 1e-8)
+def references(progs, X, y):
+    """Oracle results with error bounds in both modes: ((m, r, f, bm, br) fp32, same fp64)."""
+    return (oracle.score_bound(progs, X, y, "fp32"), oracle.score_bound(progs, X, y, "fp64"))
 
 
-def robust_set(o32, o64, progs=None, X=None, y=None, rel=1e-6):
-    m32, r32, f32 = o32
-    m64, r64, f64 = o64
-    same_flags = (f32 & FLAG_BITS) == (f64 & FLAG_BITS)
-    near = ((f32 | f64) & oracle.F_NEAR) != 0
-    rob = same_flags & ~near & close(m32, m64, rel, 1e-9) & close(r32, r64, rel, 1e-9)
-    if progs is not None:
-        from concurrent.futures import ThreadPoolExecutor
-        idx = np.nonzero(rob)[0]
-        with ThreadPoolExecutor(max(1, oracle.threads())) as ex:
-            ok = list(ex.map(lambda p: _case_bound_ok(progs, X, y, int(p), rel), idx))
-        rob[idx[~np.asarray(ok, bool)]] = False
-    return rob
-
-
-def gate(gpu, ref, mask, tol):
-    gm, gr, gf = gpu
-    om, orr, of = ref
-    flags_ok = (gf & FLAG_BITS) == (of & FLAG_BITS)
-    val_ok = close(gm, om, *tol) & close(gr, orr, *tol)
-    bad = mask & ~(flags_ok & val_ok)
-    return np.nonzero(bad)[0]
+def subset(refs, idx):
+    return tuple(tuple(a[idx] for a in r) for r in refs)
 
 
 def describe(idx, gpu, ref, limit=5):
     gm, gr, gf = gpu
-    om, orr, of = ref
     lines = []
     for i in idx[:limit]:
+        extra = f" bound=({ref[3][i]:.3g}, {ref[4][i]:.3g})" if len(ref) > 3 else ""
         lines.append(f"p={i} gpu=({gm[i]:.9g}, {gr[i]:.9g}, {gf[i]}) "
-                     f"oracle=({om[i]:.9g}, {orr[i]:.9g}, {of[i]})")
+                     f"oracle=({ref[0][i]:.9g}, {ref[1][i]:.9g}, {ref[2][i]}){extra}")
     return "\n".join(lines)
 
 
-def check_fp32(gpu, o32, o64, rob, min_robust=0.4, max_flag_mismatch=0.005):
-    """Gates A and B plus the flag rule on the robust set rob; returns its fraction."""
-    frac = float(rob.mean()) if len(rob) else 1.0
-    assert frac >= min_robust, f"robust fraction {frac:.3f} < {min_robust}"
-    a = gate(gpu, o32, rob, TOL32)
-    assert len(a) == 0, "gate A (vs FP32-ops oracle):\n" + describe(a, gpu, o32)
-    b = gate(gpu, o64, rob, TOL32)
-    assert len(b) == 0, "gate B (vs FP64 oracle):\n" + describe(b, gpu, o64)
-    nonnear = (o32[2] & oracle.F_NEAR) == 0
-    mism = nonnear & ((gpu[2] & FLAG_BITS) != (o32[2] & FLAG_BITS))
-    assert mism.mean() <= max_flag_mismatch, (
-        f"flag mismatch on {int(mism.sum())} non-NEAR programs:\n"
-        + describe(np.nonzero(mism)[0], gpu, o32))
-    return frac
+def _envelope(gpu, ref, tol, what):
+    gm, gr, gf = gpu
+    m, r, f, bm, br = ref
+    amb = (f & oracle.F_AMBIG) != 0
+    valid = (f & (oracle.F_INVALID | oracle.F_MALFORMED)) == 0
+    bad = np.nonzero(~amb & ((gf & FLAG_BITS) != (f & FLAG_BITS)))[0]
+    assert len(bad) == 0, f"{what}: flags differ\n" + describe(bad, gpu, ref)
+    env = ~amb & valid & ~(close(gm, m, *tol, extra=bm) & close(gr, r, *tol, extra=br))
+    bad = np.nonzero(env)[0]
+    assert len(bad) == 0, f"{what}: outside the error envelope\n" + describe(bad, gpu, ref)
+    return amb, valid
 
 
-def check_fp64(gpu, o32, o64, rob):
-    c = gate(gpu, o64, rob, TOL64)
-    assert len(c) == 0, "gate C (FP64 path vs FP64 oracle):\n" + describe(c, gpu, o64)
-    nonnear = (o64[2] & oracle.F_NEAR) == 0
-    mism = nonnear & ((gpu[2] & FLAG_BITS) != (o64[2] & FLAG_BITS))
-    assert mism.mean() <= 0.005, describe(np.nonzero(mism)[0], gpu, o64)
+def check_fp32(gpu, refs, min_strict=0.0):
+    """Flags, envelope and gates A/B for the FP32-compensated path."""
+    b32, b64 = refs
+    gm, gr, gf = gpu
+    amb, valid = _envelope(gpu, b32, TOL32, "FP32")
+    m, r, f, bm, br = b32
+    tight = (bm <= 1e-6 * np.abs(m) + 1e-9) & (br <= 1e-6 * np.abs(r) + 1e-9)
+    agree = close(m, b64[0], 1e-6, 1e-9) & close(r, b64[1], 1e-6, 1e-9) & \
+        ((f & FLAG_BITS) == (b64[2] & FLAG_BITS))
+    strict = ~amb & valid & tight & agree
+    for name, ref in (("A (vs FP32-ops oracle)", b32), ("B (vs FP64 oracle)", b64)):
+        ok = close(gm, ref[0], *TOL32) & close(gr, ref[1], *TOL32)
+        bad = np.nonzero(strict & ~ok)[0]
+        assert len(bad) == 0, f"gate {name}\n" + describe(bad, gpu, ref)
+    frac = float((strict | (~amb & ~valid)).mean()) if len(strict) else 1.0
+    assert frac >= min_strict, f"strict fraction {frac:.3f} < {min_strict}"
+    return {"strict": frac, "ambiguous": float(amb.mean()) if len(amb) else 0.0}
+
+
+def check_fp64(gpu, refs, min_strict=0.0):
+    """Flags, envelope and gate C for the plain FP64 path."""
+    b32, b64 = refs
+    gm, gr, gf = gpu
+    amb, valid = _envelope(gpu, b64, TOL64, "FP64")
+    m, r, f, bm, br = b64
+    tight = ~amb & valid & (bm <= 1e-13 * np.abs(m) + 1e-15) & (br <= 1e-13 * np.abs(r) + 1e-15)
+    ok = close(gm, m, *TOL64) & close(gr, r, *TOL64)
+    bad = np.nonzero(tight & ~ok)[0]
+    assert len(bad) == 0, "gate C (FP64 path vs FP64 oracle)\n" + describe(bad, gpu, b64)
+    frac = float((tight | (~amb & ~valid)).mean()) if len(tight) else 1.0
+    assert frac >= min_strict, f"strict fraction {frac:.3f} < {min_strict}"
+    return {"strict": frac}
