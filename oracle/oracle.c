@@ -412,7 +412,8 @@ uint32_t oracle_eval_bound(const uint8_t *ops, const float *cs, int32_t L, const
  *   B = sum (2 |f_i - fbar| D_i + D_i^2); r^2 = S_fy^2 / (S_ff S_yy) then stays within the
  *   interval given by the extreme corners.
  * A program whose output is constant keeps it constant on the device (every case runs the
- * same operations on the same values); its 1 - r^2 bound is 0.
+ * same operations on the same values); its 1 - r^2 bound is 0. The fp64 rounding of the
+ * aggregation (both sides aggregate in fp64) is added to the S_fy and S_ff bounds.
  */
 void oracle_fitness_bound(const double *f, const double *delta, const float *y, int64_t N,
                           uint32_t flags, double *bmse, double *bomr2) {
@@ -438,7 +439,20 @@ void oracle_fitness_bound(const double *f, const double *delta, const float *y, 
     }
     *bmse = nval(&be) / (double)N;
     if (constant) { *bomr2 = 0.0; return; }
-    const double A = nval(&ba), B = nval(&bb), Sff = nval(&sff), Syy = nval(&syy);
+    /* Rounding of the aggregation itself, in fp64 on either side: the mean carries an error
+     * of a few units of 2^-53 |f|, which moves S_ff by about N (u max|f|)^2 -- dominant
+     * when the outputs vary only in their last bits -- and each sum by a few u of its
+     * absolute terms. */
+    const double u = ldexp(1.0, -53);
+    double fmaxabs = 0.0, sfyabs = 0.0;
+    for (int64_t i = 0; i < N; ++i) {
+        fmaxabs = fmax(fmaxabs, fabs(f[i]));
+        sfyabs += fabs(f[i] - fbar) * fabs((double)y[i] - ybar);
+    }
+    const double Sff0 = nval(&sff);
+    const double A = nval(&ba) + 8.0 * u * sfyabs + 8.0 * u * fmaxabs * fabs(nval(&sy) - N * ybar);
+    const double B = nval(&bb) + 8.0 * (double)N * (u * fmaxabs) * (u * fmaxabs) + 8.0 * u * Sff0;
+    const double Sff = Sff0, Syy = nval(&syy);
     const double Sfy = fabs(nval(&sfy));
     if (!(Sff - B > 0.0)) { *bomr2 = INFINITY; return; }
     const double r2 = Sfy * Sfy / (Sff * Syy);

@@ -150,7 +150,14 @@ beagle_status beagle_upload_dataset(const float *X, const float *y, int64_t N, i
         std::memcpy(&lay[static_cast<size_t>(k) * npad], &hx[static_cast<size_t>(k) * N], N * 4);
     std::memcpy(&lay[static_cast<size_t>(d) * npad], hy.data(), N * 4);
     float *yc = &lay[static_cast<size_t>(d + 1) * npad];
-    for (int64_t i = 0; i < N; ++i) yc[i] = static_cast<float>(static_cast<double>(hy[i]) - ybar);
+    Acc syy32;
+    for (int64_t i = 0; i < N; ++i) {
+        yc[i] = static_cast<float>(static_cast<double>(hy[i]) - ybar);
+        syy32.add(static_cast<double>(yc[i]) * static_cast<double>(yc[i]));
+    }
+    // The FP32 path correlates outputs with these stored values, so its S_yy is theirs too
+    // (1 - r^2 of an exact fit then stays at rounding level instead of 2^-24).
+    ds->syy32 = syy32.value();
     // Per-tile sums of the stored centred targets, for the two tile sizes the kernels use.
     for (int which = 0; which < 2; ++which) {
         const int tile = kTileSizes[which];

@@ -118,7 +118,7 @@ beagle_status score_jobs(const JobRequest *reqs, int n, int precision, cudaStrea
         pj.dev.d = ds->d;
         pj.dev.rows = ds->rows;
         pj.dev.ybar = ds->ybar;
-        pj.dev.syy = ds->syy;
+        pj.dev.syy = precision == BEAGLE_FP64 ? ds->syy : ds->syy32;
         pj.map = &ds->map;
         max_rows = std::max(max_rows, ds->rows);
         keep.push_back(ds);

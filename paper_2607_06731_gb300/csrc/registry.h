@@ -22,6 +22,7 @@ struct Dataset {
     double *tile_sy64[2] = {nullptr, nullptr};  // same, of (double)y - ybar (FP64 path)
     CUtensorMap map;                          // box: 256 cases x rows
     double ybar = 0.0, syy = 0.0;
+    double syy32 = 0.0;                         // sum of squares of the stored fp32 y - ybar
     int holds = 0;                            // serving runs that keep it resident
     ~Dataset();
 };

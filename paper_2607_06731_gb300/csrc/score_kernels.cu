@@ -126,15 +126,15 @@ __device__ void process_program(const JobDev &J, int64_t p, int t, int tile, con
     for (int i = lane; i < nval; i += 32) {
         const T fi = fbuf[i];
         const T e = (fi - static_cast<T>(at(yrow, i))) * se_scale;
-        se.add(e * e);
+        se.add_prod(e, e);
         if (nonconst) {
             const T dv = (fi - m) * sd_scale;
             sd.add(dv);
-            sdd.add(dv * dv);
+            sdd.add_prod(dv, dv);
             // FP32: the stored fp32 y - ybar; FP64: y - ybar formed in fp64.
             const T yc = sizeof(T) == 4 ? static_cast<T>(at(ycrow, i))
                                         : static_cast<T>(at(yrow, i)) - static_cast<T>(J.ybar);
-            sdy.add(dv * (yc * sy_scale));
+            sdy.add_prod(dv, yc * sy_scale);
         }
     }
     se.warp_allreduce();
