@@ -167,6 +167,27 @@ beagle_status beagle_score_host(const uint8_t *programs, const int64_t *offsets,
                                 beagle_fitness *fitness_out, int32_t precision, void *stream);
 
 /*
+ * beagle_score_static: beagle_score that allocates no device memory. The paper has no
+ * counterpart; this is for callers that cannot allocate while they score -- a loop that must
+ * never block on the device (cudaMalloc and cudaFree may synchronise it), a process that
+ * reserves its whole device-memory budget up front, or code that runs while another
+ * component owns the allocator. Same arguments, results and asynchrony as beagle_score. Its
+ * scratch (a 256-byte header plus 44 bytes per program and case tile; tiles hold 1024 cases,
+ * 512 when d > 10 or with BEAGLE_FP64) lives in one fixed array of
+ * BEAGLE_STATIC_SCRATCH_BYTES inside the library, held on every device that loads the library
+ * until the process exits; a call that needs more fails with BEAGLE_ERR_LIMIT. The first call
+ * on a device looks up the array's device address (cudaGetSymbolAddress) with that device
+ * current, so make that first call before any stream capture. All calls share the one array
+ * and each zeroes its header on its stream: calls whose work overlaps on the GPU (other
+ * streams or threads) race, so the caller must serialise them.
+ */
+#define BEAGLE_STATIC_SCRATCH_BYTES (32u << 20)
+beagle_status beagle_score_static(const uint8_t *programs, const int64_t *offsets,
+                                  const int32_t *lengths, const float *consts, int64_t P,
+                                  int32_t dataset_id, beagle_fitness *fitness_out,
+                                  int32_t precision, void *stream);
+
+/*
  * Measurement support (not part of scoring).
  * beagle_measure_op_rates: throughput of each operator on the current device, in operator
  * evaluations per second, written to rates[opcode] for the ten arithmetic opcodes (other

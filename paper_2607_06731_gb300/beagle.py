@@ -46,6 +46,7 @@ _SIGNATURES = {
     "beagle_dataset_info": ([_i32, _vp, _vp, _vp, _vp], _i32),
     "beagle_validate_programs": ([_vp, _vp, _vp, _i64, _i32, _i32, _vp], _i32),
     "beagle_score": ([_vp, _vp, _vp, _vp, _i64, _i32, _vp, _i32, _vp], _i32),
+    "beagle_score_static": ([_vp, _vp, _vp, _vp, _i64, _i32, _vp, _i32, _vp], _i32),
     "beagle_eval": ([_vp, _vp, _vp, _vp, _i64, _i32, _vp, _vp, _i32, _vp], _i32),
     "beagle_score_host": ([_vp, _vp, _vp, _vp, _i64, _i64, _i32, _vp, _i32, _vp], _i32),
     "beagle_measure_op_rates": ([_vp, _i32, ctypes.c_double, _vp], _i32),

@@ -1,0 +1,130 @@
+// beagle_score_static: scoring that allocates no device memory.
+//
+// Some callers cannot allocate device memory while they score: a loop that must never
+// block on the device (cudaMalloc and cudaFree may synchronise it), a process that reserves
+// its whole device-memory budget up front, or code that runs while another component owns
+// the allocator. For them the scoring kernel's scratch (work counter, error word and the
+// per-(program, tile) partial sums) lives in a fixed array compiled into this library.
+#include <cstring>
+#include <mutex>
+#include <unordered_map>
+
+#include "kernels.h"
+#include "registry.h"
+
+namespace beagle {
+namespace {
+
+// Held on every device that loads this part of the library, until the process exits.
+__device__ __align__(256) unsigned char g_static_scratch[BEAGLE_STATIC_SCRATCH_BYTES];
+
+std::mutex g_static_mu;
+std::unordered_map<int, char *> g_static_addr;   // device ordinal -> device address
+
+// Device address of g_static_scratch on device dev (which must be current). In host code
+// the array's name is only a host-side stand-in, so the address is looked up once per
+// device with cudaGetSymbolAddress and cached.
+beagle_status static_scratch_address(int dev, char **out) {
+    std::lock_guard<std::mutex> lk(g_static_mu);
+    auto it = g_static_addr.find(dev);
+    if (it != g_static_addr.end()) {
+        *out = it->second;
+        return BEAGLE_OK;
+    }
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+    if (e != cudaSuccess) return cuda_fail(e, "static scratch: cudaGetSymbolAddress");
+    g_static_addr[dev] = static_cast<char *>(p);
+    *out = static_cast<char *>(p);
+    return BEAGLE_OK;
+}
+
+size_t round256(size_t x) { return (x + 255) / 256 * 256; }
+
+}  // namespace
+}  // namespace beagle
+
+using namespace beagle;
+
+extern "C" beagle_status beagle_score_static(const uint8_t *programs, const int64_t *offsets,
+                                             const int32_t *lengths, const float *consts,
+                                             int64_t P, int32_t dataset_id,
+                                             beagle_fitness *fitness_out, int32_t precision,
+                                             void *stream) {
+    if (precision != BEAGLE_FP32_COMPENSATED && precision != BEAGLE_FP64)
+        return fail(BEAGLE_ERR_ARG, "unknown precision %d", precision);
+    if (P < 0) return fail(BEAGLE_ERR_ARG, "negative P");
+    auto ds = find_dataset(dataset_id);
+    if (!ds) return fail(BEAGLE_ERR_DATASET, "unknown dataset %d", dataset_id);
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (ds->device != dev)
+        return fail(BEAGLE_ERR_DATASET, "dataset %d lives on device %d, current is %d",
+                    dataset_id, ds->device, dev);
+    if (P == 0) return BEAGLE_OK;
+    if (!programs || !offsets || !lengths || !consts || !fitness_out)
+        return fail(BEAGLE_ERR_ARG, "null pointer argument");
+
+    // Same launch plan as beagle_score for one job.
+    const int tile = (precision == BEAGLE_FP64 || ds->rows > 12) ? 512 : 1024;
+    const int32_t tiles = static_cast<int32_t>((ds->N + tile - 1) / tile);
+    const size_t part_bytes = static_cast<size_t>(kNumFields) * tiles * static_cast<size_t>(P) *
+                              sizeof(uint32_t);
+    const size_t need = 256 + round256(part_bytes);
+    if (need > BEAGLE_STATIC_SCRATCH_BYTES)
+        return fail(BEAGLE_ERR_LIMIT,
+                    "static scratch needs %zu bytes for P = %lld and %d tiles; the limit is %u "
+                    "(44 bytes per program and tile of %d cases)",
+                    need, (long long)P, tiles, (unsigned)BEAGLE_STATIC_SCRATCH_BYTES, tile);
+    char *base = nullptr;
+    beagle_status st = static_scratch_address(dev, &base);
+    if (st != BEAGLE_OK) return st;
+
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    // The array keeps the previous call's contents: the counter and error word must start
+    // at zero (the partials are fully written before they are read).
+    cudaError_t e = cudaMemsetAsync(base, 0, 256, s);
+    if (e != cudaSuccess) return cuda_fail(e, "static scratch: memset");
+
+    const int grid = sm_count();
+    const int64_t work = P * tiles;
+    const int group = static_cast<int>(
+        std::min<int64_t>(256, std::max<int64_t>(8, work / (32LL * grid))));
+    const int xbuf_floats = ds->rows * tile;
+    if (smem_bytes(precision, xbuf_floats, tile) > 227 * 1024)
+        return fail(BEAGLE_ERR_LIMIT, "shared memory plan exceeds 227 KB");
+
+    LaunchParams<1> prm;
+    std::memset(&prm, 0, sizeof prm);
+    prm.maps[0] = ds->map;
+    JobDev &J = prm.jobs[0];
+    J.ops = programs;
+    J.offs = offsets;
+    J.lens = lengths;
+    J.consts = consts;
+    J.out = fitness_out;
+    J.partials = reinterpret_cast<uint32_t *>(base + 256);
+    J.tile_sy = precision == BEAGLE_FP64 ? ds->tile_sy64[tile == 512 ? 0 : 1]
+                                         : ds->tile_sy[tile == 512 ? 0 : 1];
+    J.order = nullptr;
+    J.fout = nullptr;
+    J.P = P;
+    J.N = ds->N;
+    J.item0 = 0;
+    J.d = ds->d;
+    J.rows = ds->rows;
+    J.tiles = tiles;
+    J.groups = static_cast<int32_t>((P + group - 1) / group);
+    J.ybar = ds->ybar;
+    J.syy = precision == BEAGLE_FP64 ? ds->syy : ds->syy32;
+    prm.total_items = static_cast<int64_t>(J.groups) * tiles;
+    prm.counter = reinterpret_cast<unsigned int *>(base);
+    prm.error = reinterpret_cast<unsigned int *>(base + 128);
+    prm.njobs = 1;
+    prm.tile = tile;
+    prm.group = group;
+    prm.xbuf_floats = xbuf_floats;
+    e = launch_score(prm, precision, grid, s);
+    if (e != cudaSuccess) return cuda_fail(e, "static scoring launch");
+    return BEAGLE_OK;
+}
