@@ -172,8 +172,8 @@ beagle_status beagle_score_host(const uint8_t *programs, const int64_t *offsets,
  * never block on the device (cudaMalloc and cudaFree may synchronise it), a process that
  * reserves its whole device-memory budget up front, or code that runs while another
  * component owns the allocator. Same arguments, results and asynchrony as beagle_score. Its
- * scratch (a 256-byte header plus 44 bytes per program and case tile; tiles hold 1024 cases,
- * 512 when d > 10 or with BEAGLE_FP64) lives in one fixed array of
+ * scratch (a 256-byte header plus 44 bytes per program and case tile of 512 cases) lives in
+ * one fixed array of
  * BEAGLE_STATIC_SCRATCH_BYTES inside the library, held on every device that loads the library
  * until the process exits; a call that needs more fails with BEAGLE_ERR_LIMIT. The first call
  * on a device looks up the array's device address (cudaGetSymbolAddress) with that device

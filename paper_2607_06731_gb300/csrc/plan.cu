@@ -37,7 +37,7 @@ void keep_pool_memory(int dev) {
 
 template <int MAXJ>
 beagle_status enqueue(const std::vector<Planned> &jobs, size_t b, size_t e, int precision,
-                      int tile, int group, int grid, int xbuf_floats, cudaStream_t s) {
+                      int tile, int group, int nw, int grid, int xbuf_floats, cudaStream_t s) {
     LaunchParams<MAXJ> prm;
     std::memset(&prm, 0, sizeof prm);
     size_t scratch = 256;
@@ -71,8 +71,8 @@ beagle_status enqueue(const std::vector<Planned> &jobs, size_t b, size_t e, int 
     prm.group = group;
     prm.xbuf_floats = xbuf_floats;
     cudaError_t le;
-    if constexpr (MAXJ == 1) le = launch_score(prm, precision, grid, s);
-    else le = launch_score_batch(prm, precision, grid, s);
+    if constexpr (MAXJ == 1) le = launch_score(prm, precision, nw, grid, s);
+    else le = launch_score_batch(prm, precision, nw, grid, s);
     cudaFreeAsync(base, s);
     if (le != cudaSuccess) return cuda_fail(le, "scoring launch");
     return BEAGLE_OK;
@@ -126,9 +126,8 @@ beagle_status score_jobs(const JobRequest *reqs, int n, int precision, cudaStrea
     }
     if (jobs.empty()) return BEAGLE_OK;
 
-    // Tile: 1024 cases when two staged tiles of every job's rows fit, else 512. The FP64
-    // path keeps 512 (its per-warp output buffers hold doubles).
-    int tile = (precision == BEAGLE_FP64 || max_rows > 12) ? 512 : 1024;
+    // Tile: 512 cases (1024 on request); as many consumer warps (<= 15) as shared memory allows.
+    int tile = 512;
     if (tune && tune->tile) {
         if (tune->tile != 512 && tune->tile != 1024)
             return fail(BEAGLE_ERR_ARG, "tile must be 512 or 1024");
@@ -136,9 +135,10 @@ beagle_status score_jobs(const JobRequest *reqs, int n, int precision, cudaStrea
     }
     const int xbuf_floats = max_rows * tile;
     int grid = (tune && tune->grid) ? tune->grid : sm_count();
-    size_t smem = smem_bytes(precision, xbuf_floats, tile);
-    if (smem > 227 * 1024)
-        return fail(BEAGLE_ERR_LIMIT, "shared memory plan of %zu bytes exceeds 227 KB", smem);
+    int nw = plan_warps(precision, xbuf_floats, tile);
+    if (tune && tune->warps) nw = std::min(nw, tune->warps);
+    if (nw < 1 || smem_bytes(precision, xbuf_floats, tile, nw) > kSmemBudget)
+        return fail(BEAGLE_ERR_LIMIT, "shared memory plan exceeds %zu bytes", kSmemBudget);
     const int which = tile == 512 ? 0 : 1;
     for (size_t i = 0; i < jobs.size(); ++i) {
         JobDev &J = jobs[i].dev;
@@ -152,10 +152,10 @@ beagle_status score_jobs(const JobRequest *reqs, int n, int precision, cudaStrea
     if (tune && tune->group) group = tune->group;
 
     if (jobs.size() == 1)
-        return enqueue<1>(jobs, 0, 1, precision, tile, group, grid, xbuf_floats, s);
+        return enqueue<1>(jobs, 0, 1, precision, tile, group, nw, grid, xbuf_floats, s);
     for (size_t b = 0; b < jobs.size(); b += kMaxJobs) {
         const size_t e = std::min(jobs.size(), b + kMaxJobs);
-        beagle_status st = enqueue<kMaxJobs>(jobs, b, e, precision, tile, group, grid,
+        beagle_status st = enqueue<kMaxJobs>(jobs, b, e, precision, tile, group, nw, grid,
                                              xbuf_floats, s);
         if (st != BEAGLE_OK) return st;
     }

@@ -47,6 +47,7 @@ struct Tune {
     int group = 0;   // programs per work item
     int tile = 0;    // cases per tile (512 or 1024)
     int grid = 0;    // CTAs
+    int warps = 0;   // consumer warps per CTA (upper bound)
 };
 
 // Enqueue scoring of n jobs on stream s (one persistent launch per 64 jobs).

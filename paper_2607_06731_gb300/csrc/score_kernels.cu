@@ -6,12 +6,13 @@
 
 namespace beagle {
 
-// Shared-memory layout of one CTA (dynamic):
+// Shared-memory layout of one CTA (dynamic), nw consumer warps:
 //   [0, 64)        mbarriers: full[2], empty[2]
 //   [64, 128)      slot descriptors (2 x Slot)
 //   [128, ...)     X stage buffers: 2 x xbuf_floats fp32 (TMA destinations, 128-byte aligned)
-//   ...            per-warp output buffers: NW x tile x T
-//   ...            per-warp packed programs: NW x (kMaxLen + 2) x uint2
+//   ...            per-warp output buffers: nw x tile x T
+//   ...            per-warp packed programs: nw x (kMaxLen + 2) x uint2
+//   ...            per-warp value stacks: nw x (kMaxDepth - 1) rows x 32 K x T
 struct Slot {
     int job;        // -1: no more work
     int tile;
@@ -19,23 +20,30 @@ struct Slot {
     int next;       // next program of the item (shared-memory counter)
 };
 
-template <typename T, int K, int NW>
+template <typename T, int K>
 struct SmemLayout {
+    static constexpr size_t kStackRows = kMaxDepth - 1;
     static __host__ __device__ size_t xbuf_off() { return 128; }
     static __host__ __device__ size_t fbuf_off(int xbuf_floats) {
         return xbuf_off() + 2ull * xbuf_floats * sizeof(float);
     }
-    static __host__ __device__ size_t pbuf_off(int xbuf_floats, int tile) {
-        return fbuf_off(xbuf_floats) + static_cast<size_t>(NW) * tile * sizeof(T);
+    static __host__ __device__ size_t pbuf_off(int xbuf_floats, int tile, int nw) {
+        return fbuf_off(xbuf_floats) + static_cast<size_t>(nw) * tile * sizeof(T);
     }
-    static __host__ __device__ size_t total(int xbuf_floats, int tile) {
-        return pbuf_off(xbuf_floats, tile) + static_cast<size_t>(NW) * (kMaxLen + 2) * sizeof(uint2);
+    static __host__ __device__ size_t stack_off(int xbuf_floats, int tile, int nw) {
+        return pbuf_off(xbuf_floats, tile, nw) + static_cast<size_t>(nw) * (kMaxLen + 2) * sizeof(uint2);
+    }
+    static __host__ __device__ size_t stack_bytes_per_warp() {
+        return kStackRows * 32 * K * sizeof(T);
+    }
+    static __host__ __device__ size_t total(int xbuf_floats, int tile, int nw) {
+        return stack_off(xbuf_floats, tile, nw) + static_cast<size_t>(nw) * stack_bytes_per_warp();
     }
 };
 
 template <typename T, int K, int D>
 __device__ void process_program(const JobDev &J, int64_t p, int t, int tile, const float *xs,
-                                uint2 *pbuf, T *fbuf, int lane) {
+                                uint2 *pbuf, T *fbuf, T *stk, int lane) {
     using Sum = typename SumOf<T>::type;
     constexpr int CH = 32 * K;
     const int64_t off = J.offs[p];
@@ -61,7 +69,7 @@ __device__ void process_program(const JobDev &J, int64_t p, int t, int tile, con
         const float *xrow = xs + (c0 / kBox) * rows * kBox + (c0 % kBox) + lane * K;
         T f[K];
         bool bad[K];
-        run_program<T, K, D>(pbuf, pk.n, xrow, f, bad);
+        run_program<T, K>(pbuf, pk.n, xrow, stk + lane * K, CH, f, bad);
         T *dst = fbuf + c0 + lane * K;
 #pragma unroll
         for (int j = 0; j < K; ++j) {
@@ -172,17 +180,19 @@ __device__ __forceinline__ int find_job(const LaunchParams<MAXJ> &prm, int64_t i
     return j;
 }
 
-template <typename T, int K, int D, int NW, int MAXJ>
-__global__ void __launch_bounds__((NW + 1) * 32, 1)
+template <typename T, int K, int D, int MAXJ>
+__global__ void __launch_bounds__(kMaxThreads, 1)
 score_kernel(const __grid_constant__ LaunchParams<MAXJ> prm) {
     extern __shared__ __align__(128) unsigned char smem[];
-    using Lay = SmemLayout<T, K, NW>;
+    using Lay = SmemLayout<T, K>;
+    const int NW = static_cast<int>(blockDim.x / 32) - 1;   // consumer warps
     uint64_t *full = reinterpret_cast<uint64_t *>(smem);
     uint64_t *empty = full + 2;
     Slot *slots = reinterpret_cast<Slot *>(smem + 64);
     float *xbuf = reinterpret_cast<float *>(smem + Lay::xbuf_off());
     T *fbuf_all = reinterpret_cast<T *>(smem + Lay::fbuf_off(prm.xbuf_floats));
-    uint2 *pbuf_all = reinterpret_cast<uint2 *>(smem + Lay::pbuf_off(prm.xbuf_floats, prm.tile));
+    uint2 *pbuf_all = reinterpret_cast<uint2 *>(smem + Lay::pbuf_off(prm.xbuf_floats, prm.tile, NW));
+    T *stk_all = reinterpret_cast<T *>(smem + Lay::stack_off(prm.xbuf_floats, prm.tile, NW));
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int tile = prm.tile;
@@ -239,6 +249,7 @@ score_kernel(const __grid_constant__ LaunchParams<MAXJ> prm) {
     // Consumers
     T *fbuf = fbuf_all + static_cast<size_t>(warp) * tile;
     uint2 *pbuf = pbuf_all + static_cast<size_t>(warp) * (kMaxLen + 2);
+    T *stk = stk_all + static_cast<size_t>(warp) * (Lay::stack_bytes_per_warp() / sizeof(T));
     for (int k = 0;; ++k) {
         const int b = k & 1;
         if (!mbar_wait(&full[b], (k >> 1) & 1)) {
@@ -262,7 +273,7 @@ score_kernel(const __grid_constant__ LaunchParams<MAXJ> prm) {
             const int64_t q = p0 + idx;
             if (q >= p1) break;
             const int64_t p = J.order ? static_cast<int64_t>(J.order[q]) : q;
-            process_program<T, K, D>(J, p, s.tile, tile, xs, pbuf, fbuf, lane);
+            process_program<T, K, D>(J, p, s.tile, tile, xs, pbuf, fbuf, stk, lane);
         }
         __syncwarp();
         if (lane == 0) mbar_arrive(&empty[b]);
@@ -363,18 +374,19 @@ __global__ void finalize_kernel(const __grid_constant__ LaunchParams<MAXJ> prm) 
 }
 
 // --------------------------------------------------------------------------- launchers
-template <typename T, int K, int D, int NW, int MAXJ>
-static cudaError_t launch_impl(const LaunchParams<MAXJ> &prm, int grid, cudaStream_t stream) {
-    using Lay = SmemLayout<T, K, NW>;
-    const size_t smem = Lay::total(prm.xbuf_floats, prm.tile);
-    auto kern = score_kernel<T, K, D, NW, MAXJ>;
+template <typename T, int K, int D, int MAXJ>
+static cudaError_t launch_impl(const LaunchParams<MAXJ> &prm, int nw, int grid,
+                               cudaStream_t stream) {
+    using Lay = SmemLayout<T, K>;
+    const size_t smem = Lay::total(prm.xbuf_floats, prm.tile, nw);
+    auto kern = score_kernel<T, K, D, MAXJ>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          static_cast<int>(smem));
     if (e != cudaSuccess) return e;
     void *tok = nullptr;
     const bool timed = timing_enabled();
     if (timed) timing_begin(stream, &tok);
-    kern<<<grid, (NW + 1) * 32, smem, stream>>>(prm);
+    kern<<<grid, (nw + 1) * 32, smem, stream>>>(prm);
     e = cudaGetLastError();
     if (timed) timing_end(stream, tok);
     if (e != cudaSuccess) return e;
@@ -389,22 +401,30 @@ static cudaError_t launch_impl(const LaunchParams<MAXJ> &prm, int grid, cudaStre
     return e;
 }
 
-size_t smem_bytes(int precision, int xbuf_floats, int tile) {
-    if (precision == BEAGLE_FP64) return SmemLayout<double, kCasesFp64, kWarpsFp64>::total(xbuf_floats, tile);
-    return SmemLayout<float, kCasesFp32, kWarpsFp32>::total(xbuf_floats, tile);
+size_t smem_bytes(int precision, int xbuf_floats, int tile, int nw) {
+    if (precision == BEAGLE_FP64)
+        return SmemLayout<double, kCasesFp64>::total(xbuf_floats, tile, nw);
+    return SmemLayout<float, kCasesFp32>::total(xbuf_floats, tile, nw);
 }
 
-cudaError_t launch_score(const LaunchParams<1> &prm, int precision, int grid, cudaStream_t s) {
-    if (precision == BEAGLE_FP64)
-        return launch_impl<double, kCasesFp64, kMaxDepth, kWarpsFp64, 1>(prm, grid, s);
-    return launch_impl<float, kCasesFp32, kMaxDepth, kWarpsFp32, 1>(prm, grid, s);
+int plan_warps(int precision, int xbuf_floats, int tile) {
+    int nw = kMaxThreads / 32 - 1;
+    while (nw > 1 && smem_bytes(precision, xbuf_floats, tile, nw) > kSmemBudget) --nw;
+    return nw;
 }
 
-cudaError_t launch_score_batch(const LaunchParams<kMaxJobs> &prm, int precision, int grid,
-                               cudaStream_t s) {
+cudaError_t launch_score(const LaunchParams<1> &prm, int precision, int nw, int grid,
+                         cudaStream_t s) {
     if (precision == BEAGLE_FP64)
-        return launch_impl<double, kCasesFp64, kMaxDepth, kWarpsFp64, kMaxJobs>(prm, grid, s);
-    return launch_impl<float, kCasesFp32, kMaxDepth, kWarpsFp32, kMaxJobs>(prm, grid, s);
+        return launch_impl<double, kCasesFp64, kMaxDepth, 1>(prm, nw, grid, s);
+    return launch_impl<float, kCasesFp32, kMaxDepth, 1>(prm, nw, grid, s);
+}
+
+cudaError_t launch_score_batch(const LaunchParams<kMaxJobs> &prm, int precision, int nw,
+                               int grid, cudaStream_t s) {
+    if (precision == BEAGLE_FP64)
+        return launch_impl<double, kCasesFp64, kMaxDepth, kMaxJobs>(prm, nw, grid, s);
+    return launch_impl<float, kCasesFp32, kMaxDepth, kMaxJobs>(prm, nw, grid, s);
 }
 
 }  // namespace beagle

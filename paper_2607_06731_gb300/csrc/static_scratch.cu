@@ -66,7 +66,7 @@ extern "C" beagle_status beagle_score_static(const uint8_t *programs, const int6
         return fail(BEAGLE_ERR_ARG, "null pointer argument");
 
     // Same launch plan as beagle_score for one job.
-    const int tile = (precision == BEAGLE_FP64 || ds->rows > 12) ? 512 : 1024;
+    const int tile = 512;
     const int32_t tiles = static_cast<int32_t>((ds->N + tile - 1) / tile);
     const size_t part_bytes = static_cast<size_t>(kNumFields) * tiles * static_cast<size_t>(P) *
                               sizeof(uint32_t);
@@ -91,8 +91,9 @@ extern "C" beagle_status beagle_score_static(const uint8_t *programs, const int6
     const int group = static_cast<int>(
         std::min<int64_t>(256, std::max<int64_t>(8, work / (32LL * grid))));
     const int xbuf_floats = ds->rows * tile;
-    if (smem_bytes(precision, xbuf_floats, tile) > 227 * 1024)
-        return fail(BEAGLE_ERR_LIMIT, "shared memory plan exceeds 227 KB");
+    const int nw = plan_warps(precision, xbuf_floats, tile);
+    if (nw < 1 || smem_bytes(precision, xbuf_floats, tile, nw) > kSmemBudget)
+        return fail(BEAGLE_ERR_LIMIT, "shared memory plan exceeds %zu bytes", kSmemBudget);
 
     LaunchParams<1> prm;
     std::memset(&prm, 0, sizeof prm);
@@ -124,7 +125,7 @@ extern "C" beagle_status beagle_score_static(const uint8_t *programs, const int6
     prm.tile = tile;
     prm.group = group;
     prm.xbuf_floats = xbuf_floats;
-    e = launch_score(prm, precision, grid, s);
+    e = launch_score(prm, precision, nw, grid, s);
     if (e != cudaSuccess) return cuda_fail(e, "static scoring launch");
     return BEAGLE_OK;
 }
