@@ -49,6 +49,8 @@ _SIGNATURES = {
     "beagle_score_static": ([_vp, _vp, _vp, _vp, _i64, _i32, _vp, _i32, _vp], _i32),
     "beagle_eval": ([_vp, _vp, _vp, _vp, _i64, _i32, _vp, _vp, _i32, _vp], _i32),
     "beagle_score_host": ([_vp, _vp, _vp, _vp, _i64, _i64, _i32, _vp, _i32, _vp], _i32),
+    "beagle_set_launch_config": ([_vp], _i32),
+    "beagle_get_launch_config": ([_vp], _i32),
     "beagle_measure_op_rates": ([_vp, _i32, ctypes.c_double, _vp], _i32),
     "beagle_kernel_timing": ([_i32], _i32),
     "beagle_kernel_time": ([_vp, _vp], _i32),
@@ -264,3 +266,24 @@ def kernel_time():
     ms, n = ctypes.c_double(), ctypes.c_int64()
     check(lib().beagle_kernel_time(ctypes.byref(ms), ctypes.byref(n)))
     return ms.value, int(n.value)
+
+
+class LaunchConfig(ctypes.Structure):
+    """beagle_launch_config (0 = automatic)."""
+    _fields_ = [("cases_per_lane", ctypes.c_int32), ("tile", ctypes.c_int32),
+                ("group", ctypes.c_int32), ("warps", ctypes.c_int32), ("grid", ctypes.c_int32)]
+
+
+def set_launch_config(cases_per_lane=0, tile=0, group=0, warps=0, grid=0):
+    cfg = LaunchConfig(cases_per_lane, tile, group, warps, grid)
+    check(lib().beagle_set_launch_config(ctypes.byref(cfg)))
+
+
+def reset_launch_config():
+    check(lib().beagle_set_launch_config(None))
+
+
+def get_launch_config() -> dict:
+    cfg = LaunchConfig()
+    check(lib().beagle_get_launch_config(ctypes.byref(cfg)))
+    return {k: getattr(cfg, k) for k, _ in LaunchConfig._fields_}

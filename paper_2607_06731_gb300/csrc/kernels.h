@@ -6,25 +6,25 @@
 namespace beagle {
 
 constexpr int kMaxThreads = 512;           // 15 consumer warps + 1 producer warp at most
-constexpr int kCasesFp32 = 4;              // fitness cases per lane per pass, FP32 path
+constexpr int kCasesFp32 = 4;              // default fitness cases per lane, FP32 path (2, 4, 8)
 constexpr int kCasesFp64 = 2;              // fitness cases per lane per pass, FP64 path
 constexpr size_t kSmemBudget = 227 * 1024; // dynamic shared memory per CTA
 
-// Dynamic shared memory of one CTA with nw consumer warps.
-size_t smem_bytes(int precision, int xbuf_floats, int tile, int nw);
+// Dynamic shared memory of one CTA with nw consumer warps and `cases` cases per lane.
+size_t smem_bytes(int precision, int cases, int xbuf_floats, int tile, int nw);
 // Most consumer warps (<= 15) whose shared memory fits in kSmemBudget.
-int plan_warps(int precision, int xbuf_floats, int tile);
+int plan_warps(int precision, int cases, int xbuf_floats, int tile);
 
 // Enqueue the persistent scoring kernel (nw consumer warps + 1 producer per CTA) and the
-// finalize kernel on stream s.
-cudaError_t launch_score(const LaunchParams<1> &prm, int precision, int nw, int grid,
+// finalize kernel on stream s. `cases` (2, 4 or 8) selects the FP32 instantiation.
+cudaError_t launch_score(const LaunchParams<1> &prm, int precision, int cases, int nw, int grid,
                          cudaStream_t s);
 // Opt-in CUDA-event timing of scoring-kernel launches (beagle_kernel_timing).
 bool timing_enabled();
 void timing_begin(cudaStream_t s, void **token);
 void timing_end(cudaStream_t s, void *token);
 
-cudaError_t launch_score_batch(const LaunchParams<kMaxJobs> &prm, int precision, int nw,
-                               int grid, cudaStream_t s);
+cudaError_t launch_score_batch(const LaunchParams<kMaxJobs> &prm, int precision, int cases,
+                               int nw, int grid, cudaStream_t s);
 
 }  // namespace beagle

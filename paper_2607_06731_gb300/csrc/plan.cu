@@ -37,7 +37,8 @@ void keep_pool_memory(int dev) {
 
 template <int MAXJ>
 beagle_status enqueue(const std::vector<Planned> &jobs, size_t b, size_t e, int precision,
-                      int tile, int group, int nw, int grid, int xbuf_floats, cudaStream_t s) {
+                      int cases, int tile, int group, int nw, int grid, int xbuf_floats,
+                      cudaStream_t s) {
     LaunchParams<MAXJ> prm;
     std::memset(&prm, 0, sizeof prm);
     size_t scratch = 256;
@@ -71,8 +72,8 @@ beagle_status enqueue(const std::vector<Planned> &jobs, size_t b, size_t e, int 
     prm.group = group;
     prm.xbuf_floats = xbuf_floats;
     cudaError_t le;
-    if constexpr (MAXJ == 1) le = launch_score(prm, precision, nw, grid, s);
-    else le = launch_score_batch(prm, precision, nw, grid, s);
+    if constexpr (MAXJ == 1) le = launch_score(prm, precision, cases, nw, grid, s);
+    else le = launch_score_batch(prm, precision, cases, nw, grid, s);
     cudaFreeAsync(base, s);
     if (le != cudaSuccess) return cuda_fail(le, "scoring launch");
     return BEAGLE_OK;
@@ -126,18 +127,26 @@ beagle_status score_jobs(const JobRequest *reqs, int n, int precision, cudaStrea
     }
     if (jobs.empty()) return BEAGLE_OK;
 
-    // Tile: 512 cases (1024 on request); as many consumer warps (<= 15) as shared memory allows.
+    // Launch shape: explicit tune, else the process-wide configuration, else automatic:
+    // tile 512 cases, 4 cases per lane, as many consumer warps (<= 15) as shared memory allows.
+    Tune cfg = tune ? *tune : current_tune();
     int tile = 512;
-    if (tune && tune->tile) {
-        if (tune->tile != 512 && tune->tile != 1024)
+    if (cfg.tile) {
+        if (cfg.tile != 512 && cfg.tile != 1024)
             return fail(BEAGLE_ERR_ARG, "tile must be 512 or 1024");
-        tile = tune->tile;
+        tile = cfg.tile;
+    }
+    int cases = kCasesFp32;
+    if (cfg.cases) {
+        if (cfg.cases != 2 && cfg.cases != 4 && cfg.cases != 8)
+            return fail(BEAGLE_ERR_ARG, "cases per lane must be 2, 4 or 8");
+        cases = cfg.cases;
     }
     const int xbuf_floats = max_rows * tile;
-    int grid = (tune && tune->grid) ? tune->grid : sm_count();
-    int nw = plan_warps(precision, xbuf_floats, tile);
-    if (tune && tune->warps) nw = std::min(nw, tune->warps);
-    if (nw < 1 || smem_bytes(precision, xbuf_floats, tile, nw) > kSmemBudget)
+    int grid = cfg.grid ? cfg.grid : sm_count();
+    int nw = plan_warps(precision, cases, xbuf_floats, tile);
+    if (cfg.warps) nw = std::min(nw, cfg.warps);
+    if (nw < 1 || smem_bytes(precision, cases, xbuf_floats, tile, nw) > kSmemBudget)
         return fail(BEAGLE_ERR_LIMIT, "shared memory plan exceeds %zu bytes", kSmemBudget);
     const int which = tile == 512 ? 0 : 1;
     for (size_t i = 0; i < jobs.size(); ++i) {
@@ -149,17 +158,61 @@ beagle_status score_jobs(const JobRequest *reqs, int n, int precision, cudaStrea
     }
     // Programs per work item: about 32 items per CTA, at least 8 and at most 256 programs.
     int group = static_cast<int>(std::min<int64_t>(256, std::max<int64_t>(8, work / (32LL * grid))));
-    if (tune && tune->group) group = tune->group;
+    if (cfg.group) group = cfg.group;
 
     if (jobs.size() == 1)
-        return enqueue<1>(jobs, 0, 1, precision, tile, group, nw, grid, xbuf_floats, s);
+        return enqueue<1>(jobs, 0, 1, precision, cases, tile, group, nw, grid, xbuf_floats, s);
     for (size_t b = 0; b < jobs.size(); b += kMaxJobs) {
         const size_t e = std::min(jobs.size(), b + kMaxJobs);
-        beagle_status st = enqueue<kMaxJobs>(jobs, b, e, precision, tile, group, nw, grid,
-                                             xbuf_floats, s);
+        beagle_status st = enqueue<kMaxJobs>(jobs, b, e, precision, cases, tile, group, nw,
+                                             grid, xbuf_floats, s);
         if (st != BEAGLE_OK) return st;
     }
     return BEAGLE_OK;
 }
 
+static std::mutex g_tune_mu;
+static Tune g_tune;
+
+Tune current_tune() {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    return g_tune;
+}
+
+void set_tune(const Tune &t) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune = t;
+}
+
 }  // namespace beagle
+
+extern "C" beagle_status beagle_set_launch_config(const beagle_launch_config *cfg) {
+    beagle::Tune t;
+    if (cfg) {
+        if (cfg->cases_per_lane && cfg->cases_per_lane != 2 && cfg->cases_per_lane != 4 &&
+            cfg->cases_per_lane != 8)
+            return beagle::fail(BEAGLE_ERR_ARG, "cases_per_lane must be 0, 2, 4 or 8");
+        if (cfg->tile && cfg->tile != 512 && cfg->tile != 1024)
+            return beagle::fail(BEAGLE_ERR_ARG, "tile must be 0, 512 or 1024");
+        if (cfg->warps < 0 || cfg->warps > 15 || cfg->group < 0 || cfg->grid < 0)
+            return beagle::fail(BEAGLE_ERR_ARG, "bad launch configuration");
+        t.cases = cfg->cases_per_lane;
+        t.tile = cfg->tile;
+        t.group = cfg->group;
+        t.warps = cfg->warps;
+        t.grid = cfg->grid;
+    }
+    beagle::set_tune(t);
+    return BEAGLE_OK;
+}
+
+extern "C" beagle_status beagle_get_launch_config(beagle_launch_config *cfg) {
+    if (!cfg) return beagle::fail(BEAGLE_ERR_ARG, "null pointer argument");
+    const beagle::Tune t = beagle::current_tune();
+    cfg->cases_per_lane = t.cases;
+    cfg->tile = t.tile;
+    cfg->group = t.group;
+    cfg->warps = t.warps;
+    cfg->grid = t.grid;
+    return BEAGLE_OK;
+}

@@ -48,7 +48,11 @@ struct Tune {
     int tile = 0;    // cases per tile (512 or 1024)
     int grid = 0;    // CTAs
     int warps = 0;   // consumer warps per CTA (upper bound)
+    int cases = 0;   // fitness cases per lane, FP32 path (2, 4, 8)
 };
+
+// Process-wide launch configuration set with beagle_set_launch_config (all zero = automatic).
+Tune current_tune();
 
 // Enqueue scoring of n jobs on stream s (one persistent launch per 64 jobs).
 beagle_status score_jobs(const JobRequest *reqs, int n, int precision, cudaStream_t s,

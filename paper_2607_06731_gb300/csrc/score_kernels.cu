@@ -401,30 +401,42 @@ static cudaError_t launch_impl(const LaunchParams<MAXJ> &prm, int nw, int grid,
     return e;
 }
 
-size_t smem_bytes(int precision, int xbuf_floats, int tile, int nw) {
+size_t smem_bytes(int precision, int cases, int xbuf_floats, int tile, int nw) {
     if (precision == BEAGLE_FP64)
         return SmemLayout<double, kCasesFp64>::total(xbuf_floats, tile, nw);
-    return SmemLayout<float, kCasesFp32>::total(xbuf_floats, tile, nw);
+    switch (cases) {
+    case 2: return SmemLayout<float, 2>::total(xbuf_floats, tile, nw);
+    case 8: return SmemLayout<float, 8>::total(xbuf_floats, tile, nw);
+    default: return SmemLayout<float, 4>::total(xbuf_floats, tile, nw);
+    }
 }
 
-int plan_warps(int precision, int xbuf_floats, int tile) {
+int plan_warps(int precision, int cases, int xbuf_floats, int tile) {
     int nw = kMaxThreads / 32 - 1;
-    while (nw > 1 && smem_bytes(precision, xbuf_floats, tile, nw) > kSmemBudget) --nw;
+    while (nw > 1 && smem_bytes(precision, cases, xbuf_floats, tile, nw) > kSmemBudget) --nw;
     return nw;
 }
 
-cudaError_t launch_score(const LaunchParams<1> &prm, int precision, int nw, int grid,
-                         cudaStream_t s) {
+template <int MAXJ>
+static cudaError_t launch_any(const LaunchParams<MAXJ> &prm, int precision, int cases, int nw,
+                              int grid, cudaStream_t s) {
     if (precision == BEAGLE_FP64)
-        return launch_impl<double, kCasesFp64, kMaxDepth, 1>(prm, nw, grid, s);
-    return launch_impl<float, kCasesFp32, kMaxDepth, 1>(prm, nw, grid, s);
+        return launch_impl<double, kCasesFp64, kMaxDepth, MAXJ>(prm, nw, grid, s);
+    switch (cases) {
+    case 2: return launch_impl<float, 2, kMaxDepth, MAXJ>(prm, nw, grid, s);
+    case 8: return launch_impl<float, 8, kMaxDepth, MAXJ>(prm, nw, grid, s);
+    default: return launch_impl<float, 4, kMaxDepth, MAXJ>(prm, nw, grid, s);
+    }
 }
 
-cudaError_t launch_score_batch(const LaunchParams<kMaxJobs> &prm, int precision, int nw,
-                               int grid, cudaStream_t s) {
-    if (precision == BEAGLE_FP64)
-        return launch_impl<double, kCasesFp64, kMaxDepth, kMaxJobs>(prm, nw, grid, s);
-    return launch_impl<float, kCasesFp32, kMaxDepth, kMaxJobs>(prm, nw, grid, s);
+cudaError_t launch_score(const LaunchParams<1> &prm, int precision, int cases, int nw, int grid,
+                         cudaStream_t s) {
+    return launch_any<1>(prm, precision, cases, nw, grid, s);
+}
+
+cudaError_t launch_score_batch(const LaunchParams<kMaxJobs> &prm, int precision, int cases,
+                               int nw, int grid, cudaStream_t s) {
+    return launch_any<kMaxJobs>(prm, precision, cases, nw, grid, s);
 }
 
 }  // namespace beagle

@@ -91,8 +91,8 @@ extern "C" beagle_status beagle_score_static(const uint8_t *programs, const int6
     const int group = static_cast<int>(
         std::min<int64_t>(256, std::max<int64_t>(8, work / (32LL * grid))));
     const int xbuf_floats = ds->rows * tile;
-    const int nw = plan_warps(precision, xbuf_floats, tile);
-    if (nw < 1 || smem_bytes(precision, xbuf_floats, tile, nw) > kSmemBudget)
+    const int nw = plan_warps(precision, kCasesFp32, xbuf_floats, tile);
+    if (nw < 1 || smem_bytes(precision, kCasesFp32, xbuf_floats, tile, nw) > kSmemBudget)
         return fail(BEAGLE_ERR_LIMIT, "shared memory plan exceeds %zu bytes", kSmemBudget);
 
     LaunchParams<1> prm;
@@ -125,7 +125,7 @@ extern "C" beagle_status beagle_score_static(const uint8_t *programs, const int6
     prm.tile = tile;
     prm.group = group;
     prm.xbuf_floats = xbuf_floats;
-    e = launch_score(prm, precision, nw, grid, s);
+    e = launch_score(prm, precision, kCasesFp32, nw, grid, s);
     if (e != cudaSuccess) return cuda_fail(e, "static scoring launch");
     return BEAGLE_OK;
 }
