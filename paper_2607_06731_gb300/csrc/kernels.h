@@ -5,14 +5,15 @@
 
 namespace beagle {
 
-constexpr int kMaxThreads = 512;           // 15 consumer warps + 1 producer warp at most
+constexpr int kMaxThreads = 1024;          // 31 consumer warps + 1 producer warp at most
 constexpr int kCasesFp32 = 4;              // default fitness cases per lane, FP32 path (2, 4, 8)
 constexpr int kCasesFp64 = 2;              // fitness cases per lane per pass, FP64 path
 constexpr size_t kSmemBudget = 227 * 1024; // dynamic shared memory per CTA
 
 // Dynamic shared memory of one CTA with nw consumer warps and `cases` cases per lane.
 size_t smem_bytes(int precision, int cases, int xbuf_floats, int tile, int nw);
-// Most consumer warps (<= 15) whose shared memory fits in kSmemBudget.
+// Most consumer warps whose shared memory fits in kSmemBudget (<= 31 for variants that fit
+// in 64 registers per thread, else <= 15).
 int plan_warps(int precision, int cases, int xbuf_floats, int tile);
 
 // Enqueue the persistent scoring kernel (nw consumer warps + 1 producer per CTA) and the

@@ -194,7 +194,7 @@ extern "C" beagle_status beagle_set_launch_config(const beagle_launch_config *cf
             return beagle::fail(BEAGLE_ERR_ARG, "cases_per_lane must be 0, 2, 4 or 8");
         if (cfg->tile && cfg->tile != 512 && cfg->tile != 1024)
             return beagle::fail(BEAGLE_ERR_ARG, "tile must be 0, 512 or 1024");
-        if (cfg->warps < 0 || cfg->warps > 15 || cfg->group < 0 || cfg->grid < 0)
+        if (cfg->warps < 0 || cfg->warps > 31 || cfg->group < 0 || cfg->grid < 0)
             return beagle::fail(BEAGLE_ERR_ARG, "bad launch configuration");
         t.cases = cfg->cases_per_lane;
         t.tile = cfg->tile;

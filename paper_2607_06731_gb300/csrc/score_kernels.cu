@@ -42,8 +42,9 @@ struct SmemLayout {
 };
 
 template <typename T, int K, int D>
-__device__ void process_program(const JobDev &J, int64_t p, int t, int tile, const float *xs,
-                                uint2 *pbuf, T *fbuf, T *stk, int lane) {
+__device__ __forceinline__ void process_program(const JobDev &J, int64_t p, int t, int tile,
+                                                const float *xs, uint2 *pbuf, T *fbuf, T *stk,
+                                                int lane) {
     using Sum = typename SumOf<T>::type;
     constexpr int CH = 32 * K;
     const int64_t off = J.offs[p];
@@ -69,13 +70,12 @@ __device__ void process_program(const JobDev &J, int64_t p, int t, int tile, con
         const float *xrow = xs + (c0 / kBox) * rows * kBox + (c0 % kBox) + lane * K;
         T f[K];
         bool bad[K];
-        run_program<T, K>(pbuf, pk.n, xrow, stk + lane * K, CH, f, bad);
-        T *dst = fbuf + c0 + lane * K;
+        run_program<T, K>(smem_addr(pbuf), pk.n, smem_addr(xrow), smem_addr(stk + lane * K), f,
+                          bad);
+        sts_vec<T, K>(smem_addr(fbuf + c0 + lane * K), f);
 #pragma unroll
-        for (int j = 0; j < K; ++j) {
-            dst[j] = f[j];
+        for (int j = 0; j < K; ++j)
             if (bad[j] && c0 + lane * K + j < nval) anybad = true;
-        }
     }
     anybad = __any_sync(kFull, anybad);
     __syncwarp();
@@ -180,8 +180,13 @@ __device__ __forceinline__ int find_job(const LaunchParams<MAXJ> &prm, int64_t i
     return j;
 }
 
+template <typename T, int K>
+struct KernelThreads {   // 32 warps when a thread needs at most 64 registers, else 16
+    static constexpr int value = (sizeof(T) == 4 && K <= 4) ? 1024 : 512;
+};
+
 template <typename T, int K, int D, int MAXJ>
-__global__ void __launch_bounds__(kMaxThreads, 1)
+__global__ void __launch_bounds__(KernelThreads<T, K>::value, 1)
 score_kernel(const __grid_constant__ LaunchParams<MAXJ> prm) {
     extern __shared__ __align__(128) unsigned char smem[];
     using Lay = SmemLayout<T, K>;
@@ -411,8 +416,14 @@ size_t smem_bytes(int precision, int cases, int xbuf_floats, int tile, int nw) {
     }
 }
 
+static int max_warps(int precision, int cases) {
+    if (precision == BEAGLE_FP64) return KernelThreads<double, kCasesFp64>::value / 32 - 1;
+    if (cases == 8) return KernelThreads<float, 8>::value / 32 - 1;
+    return KernelThreads<float, 4>::value / 32 - 1;
+}
+
 int plan_warps(int precision, int cases, int xbuf_floats, int tile) {
-    int nw = kMaxThreads / 32 - 1;
+    int nw = max_warps(precision, cases);
     while (nw > 1 && smem_bytes(precision, cases, xbuf_floats, tile, nw) > kSmemBudget) --nw;
     return nw;
 }
