@@ -1,8 +1,9 @@
 // Persistent scoring kernel and the fp64 finalize kernel (see score.cuh for the design).
 #include <cstdio>
 
-#include "score.cuh"
+#include "interp_ptx.cuh"
 #include "kernels.h"
+#include "score.cuh"
 
 namespace beagle {
 
@@ -70,8 +71,12 @@ __device__ __forceinline__ void process_program(const JobDev &J, int64_t p, int 
         const float *xrow = xs + (c0 / kBox) * rows * kBox + (c0 % kBox) + lane * K;
         T f[K];
         bool bad[K];
-        run_program<T, K>(smem_addr(pbuf), pk.n, smem_addr(xrow), smem_addr(stk + lane * K), f,
-                          bad);
+        if constexpr (sizeof(T) == 4 && K == 4)
+            run_program_ptx4(smem_addr(pbuf), pk.n, smem_addr(xrow), smem_addr(stk + lane * K),
+                             f, bad);
+        else
+            run_program<T, K>(smem_addr(pbuf), pk.n, smem_addr(xrow), smem_addr(stk + lane * K),
+                              f, bad);
         sts_vec<T, K>(smem_addr(fbuf + c0 + lane * K), f);
 #pragma unroll
         for (int j = 0; j < K; ++j)
