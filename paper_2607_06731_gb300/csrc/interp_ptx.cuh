@@ -1,7 +1,7 @@
 // Interpreter loop for the FP32 path with 4 cases per lane, written in inline PTX so that the
 // token dispatch is one indexed branch (brx.idx over a .branchtargets table) instead of a
-// compare-and-branch tree. Semantics are those of run_program in score.cuh, handler for
-// handler: the same fp32 operations in the same order (.rn forms, so nothing is contracted),
+// compare-and-branch tree, and each handler dispatches the next token itself. Semantics are
+// those of run_program in score.cuh, handler for handler: the same fp32 operations in the same order (.rn forms, so nothing is contracted),
 // the same protected division and square root, the same validity tracker. sin, cos, exp and
 // the protected log leave the loop with their handler id; the caller applies them to the top
 // of stack (CUDA's sinf, cosf, expf, logf) and re-enters.
@@ -21,115 +21,106 @@ namespace beagle {
     "abs.f32 z, " DEN ";\n\tsetp.gt.f32 q, z, 0f3A83126F;\n\t"                             \
     "div.rn.f32 z, " NUM ", " DEN ";\n\tselp.f32 " DST ", z, 0f3F800000, q;\n\t"
 
-// Operands: %0-%3 top of stack (4 cases), %4-%7 validity trackers, %8/%9 current token
-// words, %10 shared address of the next token, %11 tokens left (the current one included),
-// %12 exit code (0 = done, else the transcendental handler id), %13 shared address of this
-// lane's first case of input row 0, %14 shared address of this lane's stack slot in row 0.
+// Operands: %0-%3 top of stack (4 cases), %4-%7 validity trackers, %8/%9 current token words,
+// %10/%11 next token words (prefetched), %12 shared address of the token after that, %13 exit
+// code (0 = program done, else the transcendental handler id), %14 shared address of this
+// lane's first case of input row 0, %15 shared address of this lane's slot in stack row 0.
+// Threaded dispatch: every handler ends by advancing to the prefetched token, prefetching the
+// next one and branching through the table; the program's END token leaves the loop.
+#define BG_PTX_DISPATCH                                                                    \
+    "mov.b32 %8, %10;\n\tmov.b32 %9, %11;\n\t"                                             \
+    "ld.shared.v2.u32 {%10, %11}, [%12];\n\t"                                              \
+    "add.u32 %12, %12, 8;\n\t"                                                             \
+    "and.b32 h, %8, 31;\n\t"                                                               \
+    "min.u32 h, h, 20;\n\t"                                                                \
+    "brx.idx.uni h, TBL_%=;\n"
+#define BG_PTX_ROW "bfe.u32 v, %8, 12, 8;\n\tmad.lo.u32 rp, v, 512, %15;\n\t"
+#define BG_PTX_XA "bfe.u32 v, %8, 8, 4;\n\tmad.lo.u32 xa, v, 1024, %14;\n\t"
+#define BG_PTX_S "mov.b32 s, %9;\n\t"
+
 #define BG_PTX_INTERP4                                                                     \
     "{\n\t"                                                                                \
-    ".reg .pred p, q;\n\t"                                                                 \
-    ".reg .b32 h, v, rp, xa, nx, ny;\n\t"                                                  \
+    ".reg .pred q;\n\t"                                                                    \
+    ".reg .b32 h, v, rp, xa;\n\t"                                                          \
     ".reg .f32 a0, a1, a2, a3, s, z;\n\t"                                                  \
     "TBL_%=: .branchtargets PUSHX_%=, PUSHC_%=, DUP_%=, SWAP_%=, DEL_%=, ADDSUB_%=, "      \
     "MUL_%=, PDIV_%=, SIN_%=, COS_%=, EXP_%=, PLOG_%=, PSQRT_%=, SQUARE_%=, ADDSUBX_%=, "   \
-    "MULX_%=, PDIVX_%=, ADDC_%=, MULC_%=, PDIVC_%=;\n"                                     \
-    "LOOP_%=:\n\t"                                                                         \
-    "setp.eq.s32 p, %11, 0;\n\t"                                                           \
-    "@p bra.uni DONE_%=;\n\t"                                                              \
-    "ld.shared.v2.u32 {nx, ny}, [%10];\n\t"                                                \
-    "add.u32 %10, %10, 8;\n\t"                                                             \
-    "add.s32 %11, %11, -1;\n\t"                                                            \
-    "and.b32 h, %8, 31;\n\t"                                                               \
-    "min.u32 h, h, 19;\n\t"                                                                \
-    "bfe.u32 v, %8, 12, 8;\n\t"                                                            \
-    "shl.b32 v, v, 9;\n\t"                                                                 \
-    "add.u32 rp, %14, v;\n\t"                                                              \
-    "bfe.u32 v, %8, 8, 4;\n\t"                                                             \
-    "shl.b32 v, v, 10;\n\t"                                                                \
-    "add.u32 xa, %13, v;\n\t"                                                              \
-    "mov.b32 s, %9;\n\t"                                                                   \
-    "brx.idx.uni h, TBL_%=;\n"                                                             \
-    "PUSHX_%=:\n\t"                                                                        \
+    "MULX_%=, PDIVX_%=, ADDC_%=, MULC_%=, PDIVC_%=, END_%=;\n\t"                           \
+    BG_PTX_DISPATCH                                                                        \
+    "PUSHX_%=:\n\t" BG_PTX_ROW BG_PTX_XA                                                   \
     "st.shared.v4.f32 [rp], {%0, %1, %2, %3};\n\t"                                         \
     "ld.shared.v4.f32 {%0, %1, %2, %3}, [xa];\n\t"                                         \
-    "bra.uni NEXT_%=;\n"                                                                   \
-    "PUSHC_%=:\n\t"                                                                        \
+    BG_PTX_DISPATCH                                                                        \
+    "PUSHC_%=:\n\t" BG_PTX_ROW BG_PTX_S                                                    \
     "st.shared.v4.f32 [rp], {%0, %1, %2, %3};\n\t"                                         \
     "mov.f32 %0, s;\n\tmov.f32 %1, s;\n\tmov.f32 %2, s;\n\tmov.f32 %3, s;\n\t"             \
-    "bra.uni NEXT_%=;\n"                                                                   \
-    "DUP_%=:\n\t"                                                                          \
+    BG_PTX_DISPATCH                                                                        \
+    "DUP_%=:\n\t" BG_PTX_ROW                                                               \
     "st.shared.v4.f32 [rp], {%0, %1, %2, %3};\n\t"                                         \
-    "bra.uni NEXT_%=;\n"                                                                   \
-    "SWAP_%=:\n\t"                                                                         \
+    BG_PTX_DISPATCH                                                                        \
+    "SWAP_%=:\n\t" BG_PTX_ROW                                                              \
     "ld.shared.v4.f32 {a0, a1, a2, a3}, [rp];\n\t"                                         \
     "st.shared.v4.f32 [rp], {%0, %1, %2, %3};\n\t"                                         \
     "mov.f32 %0, a0;\n\tmov.f32 %1, a1;\n\tmov.f32 %2, a2;\n\tmov.f32 %3, a3;\n\t"         \
-    "bra.uni NEXT_%=;\n"                                                                   \
-    "DEL_%=:\n\t"                                                                          \
+    BG_PTX_DISPATCH                                                                        \
+    "DEL_%=:\n\t" BG_PTX_ROW                                                               \
     "ld.shared.v4.f32 {%0, %1, %2, %3}, [rp];\n\t"                                         \
-    "bra.uni NEXT_%=;\n"                                                                   \
-    "ADDSUB_%=:\n\t"                                                                       \
+    BG_PTX_DISPATCH                                                                        \
+    "ADDSUB_%=:\n\t" BG_PTX_ROW BG_PTX_S                                                   \
     "ld.shared.v4.f32 {a0, a1, a2, a3}, [rp];\n\t"                                         \
     "fma.rn.f32 %0, s, %0, a0;\n\tfma.rn.f32 %1, s, %1, a1;\n\t"                           \
     "fma.rn.f32 %2, s, %2, a2;\n\tfma.rn.f32 %3, s, %3, a3;\n\t"                           \
-    BG_PTX_TRACK4 "bra.uni NEXT_%=;\n"                                                     \
-    "MUL_%=:\n\t"                                                                          \
+    BG_PTX_TRACK4 BG_PTX_DISPATCH                                                          \
+    "MUL_%=:\n\t" BG_PTX_ROW                                                               \
     "ld.shared.v4.f32 {a0, a1, a2, a3}, [rp];\n\t"                                         \
     "mul.rn.f32 %0, a0, %0;\n\tmul.rn.f32 %1, a1, %1;\n\t"                                 \
     "mul.rn.f32 %2, a2, %2;\n\tmul.rn.f32 %3, a3, %3;\n\t"                                 \
-    BG_PTX_TRACK4 "bra.uni NEXT_%=;\n"                                                     \
-    "PDIV_%=:\n\t"                                                                         \
+    BG_PTX_TRACK4 BG_PTX_DISPATCH                                                          \
+    "PDIV_%=:\n\t" BG_PTX_ROW                                                              \
     "ld.shared.v4.f32 {a0, a1, a2, a3}, [rp];\n\t"                                         \
     BG_PTX_PDIV("%0", "a0", "%0") BG_PTX_PDIV("%1", "a1", "%1")                            \
     BG_PTX_PDIV("%2", "a2", "%2") BG_PTX_PDIV("%3", "a3", "%3")                            \
-    BG_PTX_TRACK4 "bra.uni NEXT_%=;\n"                                                     \
-    "SIN_%=:\n\tmov.u32 %12, 8;\n\tbra.uni EXIT_%=;\n"                                     \
-    "COS_%=:\n\tmov.u32 %12, 9;\n\tbra.uni EXIT_%=;\n"                                     \
-    "EXP_%=:\n\tmov.u32 %12, 10;\n\tbra.uni EXIT_%=;\n"                                    \
-    "PLOG_%=:\n\tmov.u32 %12, 11;\n\tbra.uni EXIT_%=;\n"                                   \
+    BG_PTX_TRACK4 BG_PTX_DISPATCH                                                          \
+    "SIN_%=:\n\tmov.u32 %13, 8;\n\tbra.uni OUT_%=;\n"                                      \
+    "COS_%=:\n\tmov.u32 %13, 9;\n\tbra.uni OUT_%=;\n"                                      \
+    "EXP_%=:\n\tmov.u32 %13, 10;\n\tbra.uni OUT_%=;\n"                                     \
+    "PLOG_%=:\n\tmov.u32 %13, 11;\n\tbra.uni OUT_%=;\n"                                    \
     "PSQRT_%=:\n\t"                                                                        \
     "abs.f32 %0, %0;\n\tsqrt.rn.f32 %0, %0;\n\tabs.f32 %1, %1;\n\tsqrt.rn.f32 %1, %1;\n\t" \
     "abs.f32 %2, %2;\n\tsqrt.rn.f32 %2, %2;\n\tabs.f32 %3, %3;\n\tsqrt.rn.f32 %3, %3;\n\t" \
-    BG_PTX_TRACK4 "bra.uni NEXT_%=;\n"                                                     \
+    BG_PTX_TRACK4 BG_PTX_DISPATCH                                                          \
     "SQUARE_%=:\n\t"                                                                       \
     "mul.rn.f32 %0, %0, %0;\n\tmul.rn.f32 %1, %1, %1;\n\t"                                 \
     "mul.rn.f32 %2, %2, %2;\n\tmul.rn.f32 %3, %3, %3;\n\t"                                 \
-    BG_PTX_TRACK4 "bra.uni NEXT_%=;\n"                                                     \
-    "ADDSUBX_%=:\n\t"                                                                      \
+    BG_PTX_TRACK4 BG_PTX_DISPATCH                                                          \
+    "ADDSUBX_%=:\n\t" BG_PTX_XA BG_PTX_S                                                   \
     "ld.shared.v4.f32 {a0, a1, a2, a3}, [xa];\n\t"                                         \
     "fma.rn.f32 %0, s, a0, %0;\n\tfma.rn.f32 %1, s, a1, %1;\n\t"                           \
     "fma.rn.f32 %2, s, a2, %2;\n\tfma.rn.f32 %3, s, a3, %3;\n\t"                           \
-    BG_PTX_TRACK4 "bra.uni NEXT_%=;\n"                                                     \
-    "MULX_%=:\n\t"                                                                         \
+    BG_PTX_TRACK4 BG_PTX_DISPATCH                                                          \
+    "MULX_%=:\n\t" BG_PTX_XA                                                               \
     "ld.shared.v4.f32 {a0, a1, a2, a3}, [xa];\n\t"                                         \
     "mul.rn.f32 %0, %0, a0;\n\tmul.rn.f32 %1, %1, a1;\n\t"                                 \
     "mul.rn.f32 %2, %2, a2;\n\tmul.rn.f32 %3, %3, a3;\n\t"                                 \
-    BG_PTX_TRACK4 "bra.uni NEXT_%=;\n"                                                     \
-    "PDIVX_%=:\n\t"                                                                        \
+    BG_PTX_TRACK4 BG_PTX_DISPATCH                                                          \
+    "PDIVX_%=:\n\t" BG_PTX_XA                                                              \
     "ld.shared.v4.f32 {a0, a1, a2, a3}, [xa];\n\t"                                         \
     BG_PTX_PDIV("%0", "%0", "a0") BG_PTX_PDIV("%1", "%1", "a1")                            \
     BG_PTX_PDIV("%2", "%2", "a2") BG_PTX_PDIV("%3", "%3", "a3")                            \
-    BG_PTX_TRACK4 "bra.uni NEXT_%=;\n"                                                     \
-    "ADDC_%=:\n\t"                                                                         \
+    BG_PTX_TRACK4 BG_PTX_DISPATCH                                                          \
+    "ADDC_%=:\n\t" BG_PTX_S                                                                \
     "add.rn.f32 %0, %0, s;\n\tadd.rn.f32 %1, %1, s;\n\t"                                   \
     "add.rn.f32 %2, %2, s;\n\tadd.rn.f32 %3, %3, s;\n\t"                                   \
-    BG_PTX_TRACK4 "bra.uni NEXT_%=;\n"                                                     \
-    "MULC_%=:\n\t"                                                                         \
+    BG_PTX_TRACK4 BG_PTX_DISPATCH                                                          \
+    "MULC_%=:\n\t" BG_PTX_S                                                                \
     "mul.rn.f32 %0, %0, s;\n\tmul.rn.f32 %1, %1, s;\n\t"                                   \
     "mul.rn.f32 %2, %2, s;\n\tmul.rn.f32 %3, %3, s;\n\t"                                   \
-    BG_PTX_TRACK4 "bra.uni NEXT_%=;\n"                                                     \
-    "PDIVC_%=:\n\t"                                                                        \
+    BG_PTX_TRACK4 BG_PTX_DISPATCH                                                          \
+    "PDIVC_%=:\n\t" BG_PTX_S                                                               \
     BG_PTX_PDIV("%0", "%0", "s") BG_PTX_PDIV("%1", "%1", "s")                              \
     BG_PTX_PDIV("%2", "%2", "s") BG_PTX_PDIV("%3", "%3", "s")                              \
-    BG_PTX_TRACK4 "bra.uni NEXT_%=;\n"                                                     \
-    "NEXT_%=:\n\t"                                                                         \
-    "mov.b32 %8, nx;\n\tmov.b32 %9, ny;\n\t"                                               \
-    "bra.uni LOOP_%=;\n"                                                                   \
-    "EXIT_%=:\n\t"                                                                         \
-    "mov.b32 %8, nx;\n\tmov.b32 %9, ny;\n\t"                                               \
-    "bra.uni OUT_%=;\n"                                                                    \
-    "DONE_%=:\n\t"                                                                         \
-    "mov.u32 %12, 0;\n"                                                                    \
+    BG_PTX_TRACK4 BG_PTX_DISPATCH                                                          \
+    "END_%=:\n\tmov.u32 %13, 0;\n"                                                         \
     "OUT_%=:\n\t"                                                                          \
     "}"
 
@@ -142,18 +133,18 @@ static_assert(H_PUSHX == 0 && H_PUSHC == 1 && H_DUP == 2 && H_SWAP == 3 && H_DEL
 static_assert(StackGeom<float, 4>::kRowShift == 9 && kBoxShift == 10,
               "the PTX loop hard-codes the row and input shifts");
 
-__device__ __forceinline__ void run_program_ptx4(uint32_t prog, int n, uint32_t xrow,
-                                                 uint32_t stk, float (&top)[4], bool (&bad)[4]) {
+__device__ __forceinline__ void run_program_ptx4(uint32_t prog, uint32_t xrow, uint32_t stk,
+                                                 float (&top)[4], bool (&bad)[4]) {
     using A = Arith<float>;
     float t0 = 0.f, t1 = 0.f, t2 = 0.f, t3 = 0.f, m0 = 0.f, m1 = 0.f, m2 = 0.f, m3 = 0.f;
     const uint2 first = lds_token(prog);
-    uint32_t cx = first.x, cy = first.y, pa = prog + 8u;
-    int rem = n;
+    // The loop's first step advances to the "next" token: start with token 0 there.
+    uint32_t cx = 0u, cy = 0u, nx = first.x, ny = first.y, pa = prog + 8u;
     for (;;) {
         uint32_t code;
         asm volatile(BG_PTX_INTERP4
                      : "+f"(t0), "+f"(t1), "+f"(t2), "+f"(t3), "+f"(m0), "+f"(m1), "+f"(m2),
-                       "+f"(m3), "+r"(cx), "+r"(cy), "+r"(pa), "+r"(rem), "=r"(code)
+                       "+f"(m3), "+r"(cx), "+r"(cy), "+r"(nx), "+r"(ny), "+r"(pa), "=r"(code)
                      : "r"(xrow), "r"(stk)
                      : "memory");
         if (code == 0) break;
@@ -175,5 +166,9 @@ __device__ __forceinline__ void run_program_ptx4(uint32_t prog, int n, uint32_t 
 #undef BG_PTX_TRACK
 #undef BG_PTX_TRACK4
 #undef BG_PTX_PDIV
+#undef BG_PTX_DISPATCH
+#undef BG_PTX_ROW
+#undef BG_PTX_XA
+#undef BG_PTX_S
 
 }  // namespace beagle

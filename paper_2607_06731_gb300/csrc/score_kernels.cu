@@ -72,8 +72,7 @@ __device__ __forceinline__ void process_program(const JobDev &J, int64_t p, int 
         T f[K];
         bool bad[K];
         if constexpr (sizeof(T) == 4 && K == 4)
-            run_program_ptx4(smem_addr(pbuf), pk.n, smem_addr(xrow), smem_addr(stk + lane * K),
-                             f, bad);
+            run_program_ptx4(smem_addr(pbuf), smem_addr(xrow), smem_addr(stk + lane * K), f, bad);
         else
             run_program<T, K>(smem_addr(pbuf), pk.n, smem_addr(xrow), smem_addr(stk + lane * K),
                               f, bad);
