@@ -222,6 +222,55 @@ beagle_status beagle_measure_op_rates(double *rates, int32_t n_rates, double sec
 beagle_status beagle_kernel_timing(int32_t enable);
 beagle_status beagle_kernel_time(double *total_ms, int64_t *launches);
 
+/*
+ * Ragged batches (the paper batches populations to fit device memory, Section 2.2; here many
+ * (population, dataset) pairs share one persistent launch). A job is one beagle_score call's
+ * arguments (device pointers, as for beagle_score). Jobs may use different datasets, sizes
+ * and program lengths; programs are processed in a length-bucketed order (longest first).
+ * Results are the same bits as scoring each job alone.
+ */
+typedef struct beagle_job {
+    const uint8_t *programs;
+    const int64_t *offsets;
+    const int32_t *lengths;
+    const float *consts;
+    int64_t P;
+    int32_t dataset_id;
+    int32_t reserved;
+    beagle_fitness *fitness_out;
+} beagle_job;
+
+/* Score n_jobs jobs (host array of job descriptors) on stream; one persistent launch per 64
+ * jobs. Asynchronous. */
+beagle_status beagle_score_batch(const beagle_job *jobs, int32_t n_jobs, int32_t precision,
+                                 void *stream);
+
+/*
+ * A batch captured once into a CUDA graph and replayed: for an evolutionary loop that refills
+ * the same device buffers every generation. The plan keeps the job descriptors as given
+ * (same pointers, same sizes) and holds its datasets resident (beagle_release_dataset returns
+ * BEAGLE_ERR_BUSY until the plan is destroyed). beagle_batch_plan_launch enqueues one replay
+ * on stream (asynchronous).
+ */
+typedef struct beagle_batch_plan beagle_batch_plan;
+beagle_status beagle_batch_plan_create(const beagle_job *jobs, int32_t n_jobs,
+                                       int32_t precision, beagle_batch_plan **plan);
+beagle_status beagle_batch_plan_launch(beagle_batch_plan *plan, void *stream);
+beagle_status beagle_batch_plan_destroy(beagle_batch_plan *plan);
+
+/*
+ * Autotuner: time candidate launch shapes (cases per lane 2/4/8 x tile 512/1024 x programs per
+ * item) on the given jobs (it runs them, overwriting fitness_out) and remember the fastest for
+ * this shape class (precision, d, floor(log2 of the largest N)); later calls of that class
+ * with an automatic configuration use it. max_trials <= 0 tries all candidates. Synchronous.
+ * best / best_ms (may be NULL) receive the chosen shape and its time per call.
+ * beagle_autotune_clear forgets every tuned entry.
+ */
+beagle_status beagle_autotune(const beagle_job *jobs, int32_t n_jobs, int32_t precision,
+                              int32_t max_trials, void *stream, beagle_launch_config *best,
+                              double *best_ms);
+beagle_status beagle_autotune_clear(void);
+
 /* Message of the calling thread's most recent failure ("" if none). */
 const char *beagle_last_error(void);
 

@@ -49,6 +49,12 @@ _SIGNATURES = {
     "beagle_score_static": ([_vp, _vp, _vp, _vp, _i64, _i32, _vp, _i32, _vp], _i32),
     "beagle_eval": ([_vp, _vp, _vp, _vp, _i64, _i32, _vp, _vp, _i32, _vp], _i32),
     "beagle_score_host": ([_vp, _vp, _vp, _vp, _i64, _i64, _i32, _vp, _i32, _vp], _i32),
+    "beagle_score_batch": ([_vp, _i32, _i32, _vp], _i32),
+    "beagle_batch_plan_create": ([_vp, _i32, _i32, _vp], _i32),
+    "beagle_batch_plan_launch": ([_vp, _vp], _i32),
+    "beagle_batch_plan_destroy": ([_vp], _i32),
+    "beagle_autotune": ([_vp, _i32, _i32, _i32, _vp, _vp, _vp], _i32),
+    "beagle_autotune_clear": ([], _i32),
     "beagle_set_launch_config": ([_vp], _i32),
     "beagle_get_launch_config": ([_vp], _i32),
     "beagle_measure_op_rates": ([_vp, _i32, ctypes.c_double, _vp], _i32),
@@ -287,3 +293,62 @@ def get_launch_config() -> dict:
     cfg = LaunchConfig()
     check(lib().beagle_get_launch_config(ctypes.byref(cfg)))
     return {k: getattr(cfg, k) for k, _ in LaunchConfig._fields_}
+
+
+# ----------------------------------------------------------------------------- batches
+class Job(ctypes.Structure):
+    """beagle_job: one (population, dataset) pair of a batch (device pointers)."""
+    _fields_ = [("programs", ctypes.c_void_p), ("offsets", ctypes.c_void_p),
+                ("lengths", ctypes.c_void_p), ("consts", ctypes.c_void_p),
+                ("P", ctypes.c_int64), ("dataset_id", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("fitness_out", ctypes.c_void_p)]
+
+
+def make_jobs(items):
+    """items: sequence of (DevicePrograms, Dataset, out tensor [P, 3] float64)."""
+    arr = (Job * len(items))()
+    for i, (dp, ds, out) in enumerate(items):
+        arr[i] = Job(_ptr(dp.ops), _ptr(dp.offsets), _ptr(dp.lengths), _ptr(dp.consts), dp.P,
+                     ds.id, 0, _ptr(out))
+    return arr
+
+
+def score_batch(items, precision="fp32c", stream=None):
+    """beagle_score_batch over (DevicePrograms, Dataset, out) triples."""
+    jobs = make_jobs(items)
+    check(lib().beagle_score_batch(jobs, len(items), _precision(precision),
+                                   _stream_handle(stream)))
+
+
+class BatchPlan:
+    """beagle_batch_plan: a batch captured in a CUDA graph, replayed with launch()."""
+
+    def __init__(self, items, precision="fp32c"):
+        self._items = list(items)          # keep the buffers alive with the plan
+        jobs = make_jobs(self._items)
+        h = ctypes.c_void_p()
+        check(lib().beagle_batch_plan_create(jobs, len(self._items), _precision(precision),
+                                             ctypes.byref(h)))
+        self.handle = h
+
+    def launch(self, stream=None):
+        check(lib().beagle_batch_plan_launch(self.handle, _stream_handle(stream)))
+
+    def destroy(self):
+        if self.handle:
+            check(lib().beagle_batch_plan_destroy(self.handle))
+            self.handle = None
+
+
+def autotune(items, precision="fp32c", max_trials=0, stream=None):
+    """beagle_autotune: returns (best launch config dict, ms per call)."""
+    jobs = make_jobs(items)
+    cfg = LaunchConfig()
+    ms = ctypes.c_double()
+    check(lib().beagle_autotune(jobs, len(items), _precision(precision), max_trials,
+                                _stream_handle(stream), ctypes.byref(cfg), ctypes.byref(ms)))
+    return {k: getattr(cfg, k) for k, _ in LaunchConfig._fields_}, ms.value
+
+
+def autotune_clear():
+    check(lib().beagle_autotune_clear())

@@ -43,6 +43,14 @@ std::shared_ptr<Dataset> find_dataset(int32_t id) {
     return it == g_sets.end() ? nullptr : it->second;
 }
 
+beagle_status hold_dataset(int32_t id, int delta) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    auto it = g_sets.find(id);
+    if (it == g_sets.end()) return fail(BEAGLE_ERR_DATASET, "unknown dataset %d", id);
+    it->second->holds += delta;
+    return BEAGLE_OK;
+}
+
 Dataset::~Dataset() {
     if (data) cudaFree(data);
     if (tile_sy[0]) cudaFree(tile_sy[0]);
@@ -212,7 +220,7 @@ beagle_status beagle_release_dataset(int32_t dataset_id) {
         auto it = g_sets.find(dataset_id);
         if (it == g_sets.end()) return fail(BEAGLE_ERR_DATASET, "unknown dataset %d", dataset_id);
         if (it->second->holds > 0)
-            return fail(BEAGLE_ERR_BUSY, "dataset %d is held by %d serving run(s)", dataset_id,
+            return fail(BEAGLE_ERR_BUSY, "dataset %d is held by %d plan(s) or serving run(s)", dataset_id,
                         it->second->holds);
         ds = it->second;
         g_sets.erase(it);

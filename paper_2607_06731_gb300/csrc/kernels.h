@@ -20,6 +20,15 @@ int plan_warps(int precision, int cases, int xbuf_floats, int tile);
 // finalize kernel on stream s. `cases` (2, 4 or 8) selects the FP32 instantiation.
 cudaError_t launch_score(const LaunchParams<1> &prm, int precision, int cases, int nw, int grid,
                          cudaStream_t s);
+// Length-bucketed order of each job's programs (longest first), written to order[j].
+struct OrderParams {
+    const int32_t *lens[kMaxJobs];
+    int32_t *order[kMaxJobs];
+    int64_t P[kMaxJobs];
+    int32_t njobs;
+};
+cudaError_t launch_length_order(const OrderParams &prm, cudaStream_t s);
+
 // Opt-in CUDA-event timing of scoring-kernel launches (beagle_kernel_timing).
 bool timing_enabled();
 void timing_begin(cudaStream_t s, void **token);

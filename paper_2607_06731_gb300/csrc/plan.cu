@@ -38,11 +38,14 @@ void keep_pool_memory(int dev) {
 template <int MAXJ>
 beagle_status enqueue(const std::vector<Planned> &jobs, size_t b, size_t e, int precision,
                       int cases, int tile, int group, int nw, int grid, int xbuf_floats,
-                      cudaStream_t s) {
+                      bool sort, cudaStream_t s) {
     LaunchParams<MAXJ> prm;
     std::memset(&prm, 0, sizeof prm);
     size_t scratch = 256;
-    for (size_t i = b; i < e; ++i) scratch += up256(jobs[i].part_bytes);
+    for (size_t i = b; i < e; ++i) {
+        scratch += up256(jobs[i].part_bytes);
+        if (sort && !jobs[i].dev.order) scratch += up256(sizeof(int32_t) * jobs[i].dev.P);
+    }
     char *base = nullptr;
     cudaError_t err = cudaMallocAsync(reinterpret_cast<void **>(&base), scratch, s);
     if (err != cudaSuccess)
@@ -57,11 +60,22 @@ beagle_status enqueue(const std::vector<Planned> &jobs, size_t b, size_t e, int 
     char *cur = base + 256;
     int64_t items = 0;
     int nj = 0;
+    OrderParams op;
+    std::memset(&op, 0, sizeof op);
     for (size_t i = b; i < e; ++i, ++nj) {
         prm.maps[nj] = *jobs[i].map;
         prm.jobs[nj] = jobs[i].dev;
         prm.jobs[nj].partials = reinterpret_cast<uint32_t *>(cur);
         cur += up256(jobs[i].part_bytes);
+        if (sort && !jobs[i].dev.order) {
+            int32_t *ord = reinterpret_cast<int32_t *>(cur);
+            cur += up256(sizeof(int32_t) * jobs[i].dev.P);
+            prm.jobs[nj].order = ord;
+            op.lens[op.njobs] = jobs[i].dev.lens;
+            op.order[op.njobs] = ord;
+            op.P[op.njobs] = jobs[i].dev.P;
+            ++op.njobs;
+        }
         prm.jobs[nj].groups = static_cast<int32_t>((jobs[i].dev.P + group - 1) / group);
         prm.jobs[nj].item0 = items;
         items += static_cast<int64_t>(prm.jobs[nj].groups) * prm.jobs[nj].tiles;
@@ -71,9 +85,11 @@ beagle_status enqueue(const std::vector<Planned> &jobs, size_t b, size_t e, int 
     prm.tile = tile;
     prm.group = group;
     prm.xbuf_floats = xbuf_floats;
-    cudaError_t le;
-    if constexpr (MAXJ == 1) le = launch_score(prm, precision, cases, nw, grid, s);
-    else le = launch_score_batch(prm, precision, cases, nw, grid, s);
+    cudaError_t le = launch_length_order(op, s);
+    if (le == cudaSuccess) {
+        if constexpr (MAXJ == 1) le = launch_score(prm, precision, cases, nw, grid, s);
+        else le = launch_score_batch(prm, precision, cases, nw, grid, s);
+    }
     cudaFreeAsync(base, s);
     if (le != cudaSuccess) return cuda_fail(le, "scoring launch");
     return BEAGLE_OK;
@@ -127,9 +143,16 @@ beagle_status score_jobs(const JobRequest *reqs, int n, int precision, cudaStrea
     }
     if (jobs.empty()) return BEAGLE_OK;
 
-    // Launch shape: explicit tune, else the process-wide configuration, else automatic:
-    // tile 512 cases, 4 cases per lane, as many consumer warps (<= 15) as shared memory allows.
+    // Launch shape: explicit tune, else the process-wide configuration, else the autotuner's
+    // entry for this shape class, else automatic: tile 512 cases, 4 cases per lane, as many
+    // consumer warps as shared memory allows, programs ordered by length.
     Tune cfg = tune ? *tune : current_tune();
+    int64_t max_n = 1;
+    for (const auto &pj : jobs) max_n = std::max(max_n, pj.dev.N);
+    if (!tune && cfg.is_auto()) {
+        Tune t;
+        if (find_tuned(precision, max_rows, max_n, &t)) cfg = t;
+    }
     int tile = 512;
     if (cfg.tile) {
         if (cfg.tile != 512 && cfg.tile != 1024)
@@ -162,12 +185,14 @@ beagle_status score_jobs(const JobRequest *reqs, int n, int precision, cudaStrea
         std::min<int64_t>(256, std::max<int64_t>(2 * nw, work / (32LL * grid))));
     if (cfg.group) group = cfg.group;
 
+    const bool sort = !cfg.unsorted;
     if (jobs.size() == 1)
-        return enqueue<1>(jobs, 0, 1, precision, cases, tile, group, nw, grid, xbuf_floats, s);
+        return enqueue<1>(jobs, 0, 1, precision, cases, tile, group, nw, grid, xbuf_floats,
+                          sort, s);
     for (size_t b = 0; b < jobs.size(); b += kMaxJobs) {
         const size_t e = std::min(jobs.size(), b + kMaxJobs);
         beagle_status st = enqueue<kMaxJobs>(jobs, b, e, precision, cases, tile, group, nw,
-                                             grid, xbuf_floats, s);
+                                             grid, xbuf_floats, sort, s);
         if (st != BEAGLE_OK) return st;
     }
     return BEAGLE_OK;
@@ -175,6 +200,40 @@ beagle_status score_jobs(const JobRequest *reqs, int n, int precision, cudaStrea
 
 static std::mutex g_tune_mu;
 static Tune g_tune;
+static std::vector<std::pair<TuneKey, Tune>> g_tuned;
+
+TuneKey tune_key(int precision, int rows, int64_t max_n) {
+    int lg = 0;
+    while ((int64_t(1) << (lg + 1)) <= max_n) ++lg;
+    return TuneKey{precision, rows, lg};
+}
+
+bool find_tuned(int precision, int rows, int64_t max_n, Tune *out) {
+    const TuneKey k = tune_key(precision, rows, max_n);
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    for (const auto &e : g_tuned)
+        if (e.first == k) {
+            *out = e.second;
+            return true;
+        }
+    return false;
+}
+
+void store_tuned(int precision, int rows, int64_t max_n, const Tune &t) {
+    const TuneKey k = tune_key(precision, rows, max_n);
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    for (auto &e : g_tuned)
+        if (e.first == k) {
+            e.second = t;
+            return;
+        }
+    g_tuned.emplace_back(k, t);
+}
+
+void clear_tuned() {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tuned.clear();
+}
 
 Tune current_tune() {
     std::lock_guard<std::mutex> lk(g_tune_mu);

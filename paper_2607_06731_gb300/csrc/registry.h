@@ -28,6 +28,8 @@ struct Dataset {
 };
 
 std::shared_ptr<Dataset> find_dataset(int32_t id);
+// Add delta (+1 / -1) to a dataset's hold count (held datasets cannot be released).
+beagle_status hold_dataset(int32_t id, int delta);
 
 // One (population, dataset) pair to score.
 struct JobRequest {
@@ -49,10 +51,23 @@ struct Tune {
     int grid = 0;    // CTAs
     int warps = 0;   // consumer warps per CTA (upper bound)
     int cases = 0;   // fitness cases per lane, FP32 path (2, 4, 8)
+    int unsorted = 0;  // 1: keep the caller's program order (no length-bucketed order)
+    bool is_auto() const { return !group && !tile && !grid && !warps && !cases && !unsorted; }
 };
 
 // Process-wide launch configuration set with beagle_set_launch_config (all zero = automatic).
 Tune current_tune();
+
+// Autotuner results, keyed by shape class (precision, rows = d + 2, floor(log2(max N))).
+struct TuneKey {
+    int precision, rows, log2n;
+    bool operator==(const TuneKey &o) const {
+        return precision == o.precision && rows == o.rows && log2n == o.log2n;
+    }
+};
+bool find_tuned(int precision, int rows, int64_t max_n, Tune *out);
+void store_tuned(int precision, int rows, int64_t max_n, const Tune &t);
+void clear_tuned();
 
 // Enqueue scoring of n jobs on stream s (one persistent launch per 64 jobs).
 beagle_status score_jobs(const JobRequest *reqs, int n, int precision, cudaStream_t s,

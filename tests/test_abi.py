@@ -83,3 +83,17 @@ def test_score_rejects_unknown_dataset_without_touching_a_gpu():
     assert "unknown dataset" in beagle.last_error()
     rc = beagle.lib().beagle_score(None, None, None, None, 0, 12345, None, 7, None)
     assert rc == -1
+
+
+def test_batch_api_argument_checks_without_a_gpu():
+    assert beagle.lib().beagle_score_batch(None, -1, 0, None) == -1
+    assert beagle.lib().beagle_score_batch(None, 0, 0, None) == 0
+    jobs = beagle.Job * 1
+    arr = jobs()
+    arr[0].dataset_id = 424242
+    arr[0].P = 5
+    assert beagle.lib().beagle_score_batch(arr, 1, 0, None) == -3
+    assert beagle.lib().beagle_batch_plan_launch(None, None) == -1
+    assert beagle.lib().beagle_batch_plan_destroy(None) == 0
+    cfg = beagle.LaunchConfig(3, 0, 0, 0, 0)
+    assert beagle.lib().beagle_set_launch_config(ctypes.byref(cfg)) == -1
