@@ -191,7 +191,9 @@ beagle_status beagle_score_static(const uint8_t *programs, const int64_t *offset
  * Launch shape of the scoring kernel (no counterpart in the paper). All fields 0 = chosen
  * automatically. cases_per_lane: fitness cases each lane evaluates per pass on the FP32 path
  * (2, 4 or 8); tile: cases per staged tile (512 or 1024); group: programs per work item;
- * warps: upper bound on consumer warps per CTA (1-31); grid: CTAs (default one per SM).
+ * warps: upper bound on consumer warps per CTA (1-31); grid: CTAs (default one per SM);
+ * keep_order: 1 processes programs in the caller's order, 0 in the length-bucketed order
+ * (longest first) where the planner chooses it.
  * beagle_set_launch_config sets the process-wide configuration used by every later scoring
  * call (NULL restores automatic); results do not depend on it beyond the rounding of sums
  * over differently sized tiles (tile) -- with a fixed tile they are bit-identical.
@@ -202,6 +204,7 @@ typedef struct beagle_launch_config {
     int32_t group;
     int32_t warps;
     int32_t grid;
+    int32_t keep_order;
 } beagle_launch_config;
 beagle_status beagle_set_launch_config(const beagle_launch_config *cfg);
 beagle_status beagle_get_launch_config(beagle_launch_config *cfg);

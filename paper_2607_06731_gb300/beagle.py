@@ -277,11 +277,12 @@ def kernel_time():
 class LaunchConfig(ctypes.Structure):
     """beagle_launch_config (0 = automatic)."""
     _fields_ = [("cases_per_lane", ctypes.c_int32), ("tile", ctypes.c_int32),
-                ("group", ctypes.c_int32), ("warps", ctypes.c_int32), ("grid", ctypes.c_int32)]
+                ("group", ctypes.c_int32), ("warps", ctypes.c_int32), ("grid", ctypes.c_int32),
+                ("keep_order", ctypes.c_int32)]
 
 
-def set_launch_config(cases_per_lane=0, tile=0, group=0, warps=0, grid=0):
-    cfg = LaunchConfig(cases_per_lane, tile, group, warps, grid)
+def set_launch_config(cases_per_lane=0, tile=0, group=0, warps=0, grid=0, keep_order=0):
+    cfg = LaunchConfig(cases_per_lane, tile, group, warps, grid, keep_order)
     check(lib().beagle_set_launch_config(ctypes.byref(cfg)))
 
 

@@ -169,6 +169,7 @@ beagle_status beagle_autotune(const beagle_job *jobs, int32_t n_jobs, int32_t pr
         best->group = best_tune.group;
         best->warps = best_tune.warps;
         best->grid = best_tune.grid;
+        best->keep_order = best_tune.unsorted;
     }
     if (best_ms) *best_ms = best_t;
     return BEAGLE_OK;

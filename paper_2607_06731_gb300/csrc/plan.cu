@@ -262,6 +262,7 @@ extern "C" beagle_status beagle_set_launch_config(const beagle_launch_config *cf
         t.group = cfg->group;
         t.warps = cfg->warps;
         t.grid = cfg->grid;
+        t.unsorted = cfg->keep_order ? 1 : 0;
     }
     beagle::set_tune(t);
     return BEAGLE_OK;
@@ -275,5 +276,6 @@ extern "C" beagle_status beagle_get_launch_config(beagle_launch_config *cfg) {
     cfg->group = t.group;
     cfg->warps = t.warps;
     cfg->grid = t.grid;
+    cfg->keep_order = t.unsorted;
     return BEAGLE_OK;
 }

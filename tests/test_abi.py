@@ -95,5 +95,5 @@ def test_batch_api_argument_checks_without_a_gpu():
     assert beagle.lib().beagle_score_batch(arr, 1, 0, None) == -3
     assert beagle.lib().beagle_batch_plan_launch(None, None) == -1
     assert beagle.lib().beagle_batch_plan_destroy(None) == 0
-    cfg = beagle.LaunchConfig(3, 0, 0, 0, 0)
+    cfg = beagle.LaunchConfig(3, 0, 0, 0, 0, 0)
     assert beagle.lib().beagle_set_launch_config(ctypes.byref(cfg)) == -1
