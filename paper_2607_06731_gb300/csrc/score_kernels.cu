@@ -50,7 +50,7 @@ __device__ __forceinline__ void process_program(const JobDev &J, int64_t p, int 
     constexpr int CH = 32 * K;
     const int64_t off = J.offs[p];
     const int L = J.lens[p];
-    const Packed pk = pack_program<T, K, D>(J.ops + off, J.consts + off, L, J.d, pbuf, lane);
+    const Packed pk = pack_program<T, D>(J.ops + off, J.consts + off, L, J.d, pbuf, lane);
 
     const int64_t P = J.P;
     const int tiles = J.tiles;
@@ -71,14 +71,9 @@ __device__ __forceinline__ void process_program(const JobDev &J, int64_t p, int 
         const float *xrow = xs + (c0 / kBox) * rows * kBox + (c0 % kBox) + lane * K;
         T f[K];
         bool bad[K];
-        if constexpr (sizeof(T) == 4 && K == 4) {
-            if (c0 + CH <= nval)   // every case of the chunk exists: PTX loop, one tracker
-                run_program_ptx4(smem_addr(pbuf), smem_addr(xrow), smem_addr(stk + lane * K), f,
-                                 bad);
-            else
-                run_program<T, K>(smem_addr(pbuf), pk.n, smem_addr(xrow),
-                                  smem_addr(stk + lane * K), f, bad);
-        } else
+        if constexpr (sizeof(T) == 4 && K == 4)
+            run_program_ptx4(smem_addr(pbuf), smem_addr(xrow), smem_addr(stk + lane * K), f, bad);
+        else
             run_program<T, K>(smem_addr(pbuf), pk.n, smem_addr(xrow), smem_addr(stk + lane * K),
                               f, bad);
         sts_vec<T, K>(smem_addr(fbuf + c0 + lane * K), f);
