@@ -30,6 +30,8 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "GPoPs (node-evals/s) FP32-compensated vs plain FP64 at ≤1e-5 rel err; p50/p99"
+# kernels one scoring call launches: length order, persistent scoring kernel, fp64 finalize
+LAUNCHES_PER_CALL = 3
 WORKLOAD = ("c2-population-100k: P=100000 programs, length U{16..128}, d=5, N=1024 cases, "
             "X~U[-3,3], y=20-node expression + N(0,0.01) noise; MSE and 1-R^2")
 
@@ -45,6 +47,12 @@ def parse():
     ap.add_argument("--P", type=int, default=100_000)
     ap.add_argument("--cpu-seconds", type=float, default=10.0,
                     help="target wall time of the CPU oracle sample")
+    ap.add_argument("--workload", choices=["c2", "c3", "c4", "c5"], default="c2",
+                    help="c2: one 100k population (default, the headline line); c3: 50k "
+                         "programs x 1e6 cases, d=10 (precision); c4: 64 ragged populations "
+                         "in one graph-captured batch; c5: serving loop under Poisson load")
+    ap.add_argument("--requests", type=int, default=32,
+                    help="c5: requests per load level")
     return ap.parse_args()
 
 
@@ -120,7 +128,8 @@ def cpu_baseline(pr, seconds: float, threads: int = 0):
     import oracle
     oracle.build()
     rng = np.random.default_rng(1234)
-    n = 200
+    mean_len = float(pr.programs.lengths.mean())
+    n = int(min(pr.programs.P, max(2, min(200, 2e8 / (mean_len * pr.N)))))
     idx = rng.choice(pr.programs.P, n, replace=False)
     sub = pr.programs.subset(idx)
     t0 = time.perf_counter()
@@ -181,11 +190,246 @@ def run_reference(args, rank, world):
     return 0
 
 
+# ----------------------------------------------------------------------------- c3 / c4 / c5
+def _timed_steps(step, steps, warmup, stream, flush):
+    import torch
+    for _ in range(max(3, warmup)):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(steps)]
+    for a, b in evs:
+        flush.zero_()
+        a.record(stream)
+        step()
+        b.record(stream)
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in evs]
+
+
+def _pctl(v, q):
+    v = sorted(v)
+    return v[min(len(v) - 1, int(round(q * (len(v) - 1))))] if v else None
+
+
+def run_other_workload(args, rank, world, local):
+    """Secondary workloads, each printing its own JSON line (config.workload names it)."""
+    import __graft_entry__
+    __graft_entry__.build()
+    import torch
+    from paper_2607_06731_gb300 import beagle, synth
+    torch.cuda.set_device(local)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    rates = beagle.measure_op_rates(1.0, stream=stream)
+    clocks = Clocks(local)
+    base = {"metric": METRIC, "unit": "GPoPs", "n_gpus": world, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic"}
+    if args.workload == "c3":
+        line = _run_c3(args, beagle, synth, torch, stream, flush, rates, clocks)
+    elif args.workload == "c4":
+        line = _run_c4(args, beagle, synth, torch, stream, flush, rates, clocks)
+    else:
+        line = _run_c5(args, beagle, synth, torch, stream, rates, clocks)
+    if rank == 0:
+        print(json.dumps({**base, **line}), flush=True)
+    return 0
+
+
+def _run_c3(args, beagle, synth, torch, stream, flush, rates, clocks):
+    """50,000 programs (length U{16..64}) x 1e6 cases, d = 10, y of RMS 1e3: the precision
+    workload. FP32-compensated and plain FP64 paths, error of the first against the second."""
+    pr = synth.make_c3()
+    ds = beagle.Dataset(pr.X, pr.y)
+    dp = beagle.DevicePrograms(pr.programs)
+    out = torch.empty((dp.P, 3), dtype=torch.float64, device="cuda")
+    clocks.start()
+    beagle.kernel_timing(True)
+    beagle.kernel_time()
+    ms = _timed_steps(lambda: beagle.score_programs(dp, ds, out=out, stream=stream),
+                      args.steps, args.warmup, stream, flush)
+    clk = clocks.stop()
+    beagle.kernel_timing(False)
+    kern_ms, kern_n = beagle.kernel_time()
+    f32 = beagle.unpack_fitness(out)
+    ms64 = _timed_steps(lambda: beagle.score_programs(dp, ds, out=out, precision="fp64",
+                                                      stream=stream),
+                        max(1, args.fp64_steps), 0, stream, flush)
+    f64 = beagle.unpack_fitness(out)
+    ok = ((f32[2] & 5) == 0) & ((f64[2] & 5) == 0)
+    err = {}
+    for k, name in ((0, "mse"), (1, "one_minus_r2")):
+        a, b = f32[k][ok], f64[k][ok]
+        rel = np.abs(a - b) / np.maximum(np.abs(b), 1e-300)
+        err[name] = {"frac_within_1e-5": float(np.mean(np.abs(a - b) <=
+                                                        np.maximum(1e-5 * np.abs(b), 1e-7))),
+                     "median_rel": float(np.median(rel)), "max_rel": float(rel.max())}
+    ev = pr.node_evals
+    kern_s = kern_ms / max(kern_n, 1) / 1e3
+    peak = ev / roofline_peak(pr.programs, pr.N, rates) / 1e9
+    return {"value": ev * len(ms) / (sum(ms) / 1e3) / 1e9, "steps": len(ms),
+            "warmup": max(3, args.warmup), "ms_per_step": statistics.mean(ms),
+            "p50_ms": _pctl(ms, 0.5), "p99_ms": _pctl(ms, 0.99),
+            "config": {"workload": "c3-precision-1m: P=50000 programs, length U{16..64}, "
+                                   "d=10, N=1000000 cases, X~N(0,1), y RMS 1e3 + N(0,1)",
+                       "P": dp.P, "N": pr.N, "d": pr.d, "node_evals_per_step": ev,
+                       "l2": "inputs (40 MB X) plus a 256 MiB flush before every step"},
+            "fp64": {"value": ev / (statistics.median(ms64) / 1e3) / 1e9, "unit": "GPoPs",
+                     "ms_per_step": statistics.median(ms64)},
+            "fp32c_error_vs_fp64_path": {"programs_compared": int(ok.sum()), **err},
+            "roofline": {"bound": "alu", "achieved": ev / kern_s / 1e9, "peak": peak,
+                         "unit": "GPoPs", "frac": ev / kern_s / 1e9 / peak, "traffic": None},
+            "cpu_baseline": cpu_baseline(pr, args.cpu_seconds),
+            "gpu_launches": LAUNCHES_PER_CALL * len(ms), "clocks": clk}
+
+
+def _run_c4(args, beagle, synth, torch, stream, flush, rates, clocks):
+    """64 ragged populations (P log-U[1e3, 2e5], L U{4..256}, N log-U[256, 1e5], d U{1..10}),
+    each with its own resident dataset, scored in one graph-captured persistent batch; the
+    same populations scored one call each for comparison."""
+    pops = synth.make_c4()
+    items = []
+    for pr in pops:
+        ds = beagle.Dataset(pr.X, pr.y)
+        dp = beagle.DevicePrograms(pr.programs)
+        items.append((dp, ds, torch.empty((dp.P, 3), dtype=torch.float64, device="cuda")))
+    ev = sum(pr.node_evals for pr in pops)
+    plan = beagle.BatchPlan(items)
+    clocks.start()
+    ms = _timed_steps(lambda: plan.launch(stream), args.steps, args.warmup, stream, flush)
+    clk = clocks.stop()
+    # kernel time of the scoring kernel: the same batch launched uncaptured (graph replays
+    # bypass the library's launch hooks)
+    beagle.kernel_timing(True)
+    beagle.kernel_time()
+    for _ in range(2):
+        flush.zero_()
+        beagle.score_batch(items, stream=stream)
+    torch.cuda.synchronize()
+    beagle.kernel_timing(False)
+    kern_ms, kern_n = beagle.kernel_time()
+
+    def one_by_one():
+        for dp, ds, out in items:
+            beagle.score_programs(dp, ds, out=out, stream=stream)
+    ms1 = _timed_steps(one_by_one, max(1, min(3, args.steps)), 1, stream, flush)
+    t_roof = sum(roofline_peak(pr.programs, pr.N, rates) for pr in pops)
+    launches_per_plan = (len(items) + 63) // 64 * LAUNCHES_PER_CALL
+    kern_s = kern_ms / 1e3 / 2                   # scoring-kernel time per batch
+    big = max(pops, key=lambda p: p.node_evals)
+    return {"value": ev * len(ms) / (sum(ms) / 1e3) / 1e9, "steps": len(ms),
+            "warmup": max(3, args.warmup), "ms_per_step": statistics.mean(ms),
+            "p50_ms": _pctl(ms, 0.5), "p99_ms": _pctl(ms, 0.99),
+            "config": {"workload": "c4-ragged-64: 64 populations, P log-U[1e3,2e5], "
+                                   "L U{4..256}, N log-U[256,1e5], d U{1..10}, one dataset "
+                                   "each; one graph-captured batch per step",
+                       "populations": len(pops), "programs": int(sum(p.programs.P for p in pops)),
+                       "node_evals_per_step": ev,
+                       "l2": "256 MiB flush before every step"},
+            "one_call_per_population": {"value": ev / (statistics.median(ms1) / 1e3) / 1e9,
+                                        "unit": "GPoPs", "ms_per_step": statistics.median(ms1)},
+            "roofline": {"bound": "alu", "achieved": ev / kern_s / 1e9 if kern_s else None,
+                         "peak": ev / t_roof / 1e9, "unit": "GPoPs",
+                         "frac": (ev / kern_s / 1e9) / (ev / t_roof / 1e9) if kern_s else None,
+                         "traffic": None, "kernel_launches_timed": kern_n},
+            "cpu_baseline": cpu_baseline(big, args.cpu_seconds),
+            "gpu_launches": launches_per_plan * len(ms), "clocks": clk}
+
+
+def _run_c5(args, beagle, synth, torch, stream, rates, clocks):
+    """Serving: 16 evolutionary runs with resident datasets submit generations (P log-U[1e4,
+    5e5], L U{8..200}) to one server; first at once (capacity), then as Poisson arrivals at
+    0.5x, 0.9x and 1.2x of that capacity. Reports GPoPs and p50 / p99 latency per level.
+    Request populations are slices of one 100k-program population per input count d (cycled
+    where a request asks for more), generated before timing."""
+    runs = synth.make_serving_runs()
+    dsets = [beagle.Dataset(r["X"], r["y"]) for r in runs]
+    pools = {}
+    for r in runs:
+        if r["d"] not in pools:
+            pools[r["d"]] = synth.gen_programs(np.random.default_rng([5, 3, r["d"]]), 100_000,
+                                               8, 200, r["d"])
+    rng = np.random.default_rng([5, 4])
+
+    def make_requests(n):
+        reqs = []
+        for k in range(n):
+            run = int(rng.integers(len(runs)))
+            pool = pools[runs[run]["d"]]
+            P = int(np.exp(rng.uniform(np.log(1e4), np.log(5e5))))
+            start = int(rng.integers(pool.P))
+            progs = pool.subset((start + np.arange(P)) % pool.P)
+            reqs.append((run, progs, int(progs.lengths.sum()) * runs[run]["N"]))
+        return reqs
+
+    def serve(reqs, rate_rps):
+        srv = beagle.Server()
+        res = []
+        t0 = time.perf_counter()
+
+        tickets = []
+        arr = np.cumsum(rng.exponential(1.0 / rate_rps, len(reqs))) if rate_rps else None
+        for k, (run, progs, _) in enumerate(reqs):
+            if arr is not None:
+                dt = t0 + arr[k] - time.perf_counter()
+                if dt > 0:
+                    time.sleep(dt)
+            tickets.append(srv.submit(progs, dsets[run]))
+        for t in tickets:        # latency is measured by the server (submit to result)
+            res.append(srv.wait(t))
+        wall = time.perf_counter() - t0
+        st = srv.stats()
+        srv.destroy()
+        return wall, st
+
+    warm = make_requests(4)
+    serve(warm, 0)
+    reqs = make_requests(args.requests)
+    ev = sum(r[2] for r in reqs)
+    clocks.start()
+    wall, st = serve(reqs, 0)
+    cap_rps = len(reqs) / wall
+    levels = {}
+    for f in (0.5, 0.9, 1.2):
+        reqs_f = make_requests(args.requests)
+        w, s2 = serve(reqs_f, f * cap_rps)
+        levels[f"{f}x"] = {"offered_rps": f * cap_rps, "gpops": s2["gpops"],
+                           "p50_ms": s2["p50_us"] / 1e3, "p99_ms": s2["p99_us"] / 1e3,
+                           "max_ms": s2["max_us"] / 1e3, "launches": s2["launches"],
+                           "peak_gb": s2["peak_bytes"] / 1e9}
+    clk = clocks.stop()
+    ex = make_requests(1)[0]
+    pr = synth.Problem("c5-sample", ex[1], runs[ex[0]]["X"], runs[ex[0]]["y"], {})
+    return {"value": st["gpops"], "steps": len(reqs), "warmup": len(warm),
+            "ms_per_step": wall / len(reqs) * 1e3,
+            "p50_ms": st["p50_us"] / 1e3, "p99_ms": st["p99_us"] / 1e3,
+            "config": {"workload": "c5-serving: 16 runs with resident datasets (N log-U[512,"
+                                   "65536], d U{1..10}); requests P log-U[1e4,5e5], "
+                                   "L U{8..200}; closed loop, then Poisson at 0.5/0.9/1.2x",
+                       "requests_per_level": len(reqs), "node_evals_closed_loop": ev,
+                       "budget_bytes": st["budget_bytes"],
+                       "l2": "inputs larger than L2 per request"},
+            "closed_loop": {"requests_per_s": cap_rps, "launches": st["launches"],
+                            "peak_gb": st["peak_bytes"] / 1e9},
+            "poisson": levels,
+            "e2e": {"value": st["gpops"], "unit": "GPoPs",
+                    "h2d_bytes_per_step": int(np.mean([r[1].ops.nbytes * 5 + r[1].P * 12
+                                                       for r in reqs])),
+                    "d2h_bytes_per_step": int(np.mean([r[1].P * 24 for r in reqs]))},
+            "roofline": None,
+            "cpu_baseline": cpu_baseline(pr, args.cpu_seconds),
+            "gpu_launches": st["launches"] * LAUNCHES_PER_CALL, "clocks": clk}
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
     if args.impl == "reference":
         return run_reference(args, rank, world)
+
+    if args.workload != "c2":
+        return run_other_workload(args, rank, world, local)
 
     import __graft_entry__
     __graft_entry__.build()
@@ -324,7 +568,7 @@ def main():
         "cpu_baseline": cpu,
         "e2e": {"value": node_evals / statistics.median(e2e_s) / 1e9, "unit": "GPoPs",
                 "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
-        "gpu_launches": 2 * args.steps,
+        "gpu_launches": LAUNCHES_PER_CALL * args.steps,
         "clocks": clk,
         "op_rates_gevals": {str(k): v / 1e9 for k, v in sorted(rates.items())},
     }

@@ -188,6 +188,62 @@ beagle_status beagle_score_static(const uint8_t *programs, const int64_t *offset
                                   int32_t precision, void *stream);
 
 /*
+ * Serving (continuous batching). Many concurrent evolutionary runs each submit one generation
+ * at a time -- a population in the wire format in HOST memory, scored against the run's
+ * resident dataset (Section 2.4: genomes go to the device once per generation, one fitness per
+ * genome comes back). The server copies each request into pinned staging recycled from a
+ * pool (Section 2.7's dead pool), admits queued requests in arrival order while their device
+ * bytes (inputs, outputs and scoring scratch) fit hbm_budget_bytes and a stream is free, packs
+ * every admitted request into one persistent launch (one job each), and lets requests that
+ * arrive meanwhile form the next launch on another stream. A request's results are the same
+ * bits alone and in any mix. Datasets are held resident while a request uses them.
+ *   submit   non-blocking; returns a ticket. A request larger than the budget fails with
+ *            BEAGLE_ERR_OOM when it reaches the head of the queue.
+ *   poll     *done = 1 and the results copied to host_out (P records) once finished; the
+ *            ticket is then retired.
+ *   wait     blocks until finished (timeout_us < 0: no limit); BEAGLE_ERR_TIMEOUT if not done
+ *            in time (the ticket stays valid); on success retires the ticket.
+ *   stats    counters, node evaluations per second between the first submission and the last
+ *            completion, and p50 / p99 / max latency (submit to result) of completed requests.
+ *   destroy  finishes every queued and running request, then frees the server.
+ */
+typedef struct beagle_serve_config {
+    int64_t hbm_budget_bytes;   /* 0: half of the free device memory at creation */
+    int32_t max_inflight;       /* launches in flight at once (streams), 1-8; 0: 2 */
+    int32_t max_batch_jobs;     /* requests packed into one launch; 0: 64 */
+    int32_t precision;          /* BEAGLE_FP32_COMPENSATED or BEAGLE_FP64 */
+    int32_t reserved;
+} beagle_serve_config;
+
+typedef struct beagle_request {
+    const uint8_t *programs;    /* host, as for beagle_score */
+    const int64_t *offsets;
+    const int32_t *lengths;
+    const float *consts;
+    int64_t P;
+    int64_t n_tokens;           /* total tokens (length of programs and consts) */
+    int32_t dataset_id;
+    int32_t reserved;
+} beagle_request;
+
+typedef struct beagle_serve_counters {
+    int64_t submitted, completed, rejected, queued, inflight_launches, launches;
+    int64_t node_evals, bytes_in_use, peak_bytes, budget_bytes;
+    double gpops, p50_us, p99_us, max_us;
+} beagle_serve_counters;
+
+typedef struct beagle_server beagle_server;
+beagle_status beagle_serve_create(const beagle_serve_config *cfg, beagle_server **server);
+beagle_status beagle_serve_submit(beagle_server *server, const beagle_request *req,
+                                  uint64_t *ticket);
+beagle_status beagle_serve_poll(beagle_server *server, uint64_t ticket,
+                                beagle_fitness *host_out, int32_t *done);
+beagle_status beagle_serve_wait(beagle_server *server, uint64_t ticket,
+                                beagle_fitness *host_out, int64_t timeout_us);
+beagle_status beagle_serve_stats(beagle_server *server, beagle_serve_counters *stats);
+beagle_status beagle_serve_destroy(beagle_server *server);
+
+/*
  * Launch shape of the scoring kernel (no counterpart in the paper). All fields 0 = chosen
  * automatically. cases_per_lane: fitness cases each lane evaluates per pass on the FP32 path
  * (2, 4 or 8); tile: cases per staged tile (512 or 1024); group: programs per work item;

@@ -16,6 +16,8 @@ import numpy as np
 from . import build as _build
 
 OK = 0
+ERR_OOM = -4
+ERR_TIMEOUT = -6
 ERRORS = {-1: "BEAGLE_ERR_ARG", -2: "BEAGLE_ERR_PROGRAM", -3: "BEAGLE_ERR_DATASET",
           -4: "BEAGLE_ERR_OOM", -5: "BEAGLE_ERR_CUDA", -6: "BEAGLE_ERR_TIMEOUT",
           -7: "BEAGLE_ERR_BUSY", -8: "BEAGLE_ERR_LIMIT"}
@@ -55,6 +57,12 @@ _SIGNATURES = {
     "beagle_batch_plan_destroy": ([_vp], _i32),
     "beagle_autotune": ([_vp, _i32, _i32, _i32, _vp, _vp, _vp], _i32),
     "beagle_autotune_clear": ([], _i32),
+    "beagle_serve_create": ([_vp, _vp], _i32),
+    "beagle_serve_submit": ([_vp, _vp, _vp], _i32),
+    "beagle_serve_poll": ([_vp, ctypes.c_uint64, _vp, _vp], _i32),
+    "beagle_serve_wait": ([_vp, ctypes.c_uint64, _vp, _i64], _i32),
+    "beagle_serve_stats": ([_vp, _vp], _i32),
+    "beagle_serve_destroy": ([_vp], _i32),
     "beagle_set_launch_config": ([_vp], _i32),
     "beagle_get_launch_config": ([_vp], _i32),
     "beagle_measure_op_rates": ([_vp, _i32, ctypes.c_double, _vp], _i32),
@@ -353,3 +361,82 @@ def autotune(items, precision="fp32c", max_trials=0, stream=None):
 
 def autotune_clear():
     check(lib().beagle_autotune_clear())
+
+
+# ----------------------------------------------------------------------------- serving
+class ServeConfig(ctypes.Structure):
+    _fields_ = [("hbm_budget_bytes", ctypes.c_int64), ("max_inflight", ctypes.c_int32),
+                ("max_batch_jobs", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+class Request(ctypes.Structure):
+    _fields_ = [("programs", ctypes.c_void_p), ("offsets", ctypes.c_void_p),
+                ("lengths", ctypes.c_void_p), ("consts", ctypes.c_void_p),
+                ("P", ctypes.c_int64), ("n_tokens", ctypes.c_int64),
+                ("dataset_id", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class ServeStats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int64) for n in
+                ("submitted", "completed", "rejected", "queued", "inflight_launches",
+                 "launches", "node_evals", "bytes_in_use", "peak_bytes", "budget_bytes")] + \
+               [(n, ctypes.c_double) for n in ("gpops", "p50_us", "p99_us", "max_us")]
+
+
+class Server:
+    """beagle_serve_*: continuous-batching scoring server (host-memory requests)."""
+
+    def __init__(self, hbm_budget_bytes=0, max_inflight=0, max_batch_jobs=0,
+                 precision="fp32c"):
+        cfg = ServeConfig(hbm_budget_bytes, max_inflight, max_batch_jobs,
+                          _precision(precision), 0)
+        h = ctypes.c_void_p()
+        check(lib().beagle_serve_create(ctypes.byref(cfg), ctypes.byref(h)))
+        self.handle = h
+        self._keep = {}
+
+    def submit(self, progs, dataset: "Dataset") -> int:
+        ops = np.ascontiguousarray(progs.ops, np.uint8)
+        offs = np.ascontiguousarray(progs.offsets, np.int64)
+        lens = np.ascontiguousarray(progs.lengths, np.int32)
+        cs = np.ascontiguousarray(progs.consts, np.float32)
+        req = Request(_ptr(ops), _ptr(offs), _ptr(lens), _ptr(cs), len(lens), len(ops),
+                      dataset.id, 0)
+        t = ctypes.c_uint64()
+        check(lib().beagle_serve_submit(self.handle, ctypes.byref(req), ctypes.byref(t)))
+        self._keep[t.value] = len(lens)
+        return t.value
+
+    def poll(self, ticket: int):
+        """None while running, else the structured fitness array."""
+        P = self._keep[ticket]
+        out = np.zeros(P, FITNESS_DTYPE)
+        done = ctypes.c_int32()
+        rc = lib().beagle_serve_poll(self.handle, ticket, _ptr(out) if P else None,
+                                     ctypes.byref(done))
+        if rc == OK and not done.value:
+            return None
+        self._keep.pop(ticket, None)   # finished (or failed): the ticket is retired
+        check(rc)
+        return out
+
+    def wait(self, ticket: int, timeout_us: int = -1):
+        P = self._keep[ticket]
+        out = np.zeros(P, FITNESS_DTYPE)
+        rc = lib().beagle_serve_wait(self.handle, ticket, _ptr(out) if P else None,
+                                     timeout_us)
+        if rc != ERR_TIMEOUT:
+            self._keep.pop(ticket, None)   # a timed-out ticket stays valid
+        check(rc)
+        return out
+
+    def stats(self) -> dict:
+        st = ServeStats()
+        check(lib().beagle_serve_stats(self.handle, ctypes.byref(st)))
+        return {k: getattr(st, k) for k, _ in ServeStats._fields_}
+
+    def destroy(self):
+        if self.handle:
+            check(lib().beagle_serve_destroy(self.handle))
+            self.handle = None

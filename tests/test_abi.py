@@ -97,3 +97,21 @@ def test_batch_api_argument_checks_without_a_gpu():
     assert beagle.lib().beagle_batch_plan_destroy(None) == 0
     cfg = beagle.LaunchConfig(3, 0, 0, 0, 0, 0)
     assert beagle.lib().beagle_set_launch_config(ctypes.byref(cfg)) == -1
+
+
+def test_serve_api_argument_checks_without_a_gpu():
+    L = beagle.lib()
+    assert L.beagle_serve_create(None, None) == -1
+    cfg = beagle.ServeConfig(1 << 20, 2, 8, 7, 0)
+    h = ctypes.c_void_p()
+    assert L.beagle_serve_create(ctypes.byref(cfg), ctypes.byref(h)) == -1
+    assert "precision" in beagle.last_error()
+    cfg = beagle.ServeConfig(1 << 20, 9, 8, 0, 0)
+    assert L.beagle_serve_create(ctypes.byref(cfg), ctypes.byref(h)) == -8
+    assert L.beagle_serve_submit(None, None, None) == -1
+    assert L.beagle_serve_stats(None, None) == -1
+    assert L.beagle_serve_wait(None, 1, None, 0) == -1
+    assert L.beagle_serve_destroy(None) == 0
+    assert ctypes.sizeof(beagle.ServeConfig) == 24
+    assert ctypes.sizeof(beagle.Request) == 56
+    assert ctypes.sizeof(beagle.ServeStats) == 10 * 8 + 4 * 8
