@@ -299,8 +299,10 @@ typedef struct beagle_job {
     beagle_fitness *fitness_out;
 } beagle_job;
 
-/* Score n_jobs jobs (host array of job descriptors) on stream; one persistent launch per 64
- * jobs. Asynchronous. */
+/* Score n_jobs jobs (host array of job descriptors) on stream. Jobs are grouped into
+ * persistent launches of at most 64 jobs, in ascending order of input count d; a launch is
+ * cut where d changes once it holds 2^24 program-cases (sum of P x N), since its shared memory
+ * is sized by its widest dataset. Asynchronous. */
 beagle_status beagle_score_batch(const beagle_job *jobs, int32_t n_jobs, int32_t precision,
                                  void *stream);
 

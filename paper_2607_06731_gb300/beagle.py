@@ -410,7 +410,7 @@ class Server:
 
     def poll(self, ticket: int):
         """None while running, else the structured fitness array."""
-        P = self._keep[ticket]
+        P = self._keep.get(ticket, 0)     # unknown tickets: the library reports the error
         out = np.zeros(P, FITNESS_DTYPE)
         done = ctypes.c_int32()
         rc = lib().beagle_serve_poll(self.handle, ticket, _ptr(out) if P else None,
@@ -422,7 +422,7 @@ class Server:
         return out
 
     def wait(self, ticket: int, timeout_us: int = -1):
-        P = self._keep[ticket]
+        P = self._keep.get(ticket, 0)
         out = np.zeros(P, FITNESS_DTYPE)
         rc = lib().beagle_serve_wait(self.handle, ticket, _ptr(out) if P else None,
                                      timeout_us)

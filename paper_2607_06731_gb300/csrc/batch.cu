@@ -59,6 +59,11 @@ beagle_status beagle_batch_plan_create(const beagle_job *jobs, int32_t n_jobs, i
         }
         pl->held.push_back(r.dataset_id);
     }
+    st = prepare_capture();
+    if (st != BEAGLE_OK) {
+        beagle_batch_plan_destroy(pl);
+        return st;
+    }
     cudaStream_t s = nullptr;
     cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);

@@ -2,7 +2,9 @@
 // token dispatch is one indexed branch (brx.idx over a .branchtargets table) instead of a
 // compare-and-branch tree, and each handler dispatches the next token itself. Semantics are
 // those of run_program in score.cuh, handler for handler: the same fp32 operations in the same order (.rn forms, so nothing is contracted),
-// the same protected division and square root, the same validity tracker. sin, cos, exp and
+// the same protected division and square root, the same validity decisions (the tracker
+// skips the protected square root, sin, cos and the protected log, whose results are finite
+// and at most 1e15 in magnitude whenever their operand is valid). sin, cos, exp and
 // the protected log leave the loop with their handler id; the caller applies them to the top
 // of stack (CUDA's sinf, cosf, expf, logf) and re-enters.
 #pragma once
@@ -27,12 +29,15 @@ namespace beagle {
 // lane's first case of input row 0, %15 shared address of this lane's slot in stack row 0.
 // Threaded dispatch: every handler ends by advancing to the prefetched token, prefetching the
 // next one and branching through the table; the program's END token leaves the loop.
+// The table has 32 entries (ids 21-31 end the program), so the 5-bit handler field needs no
+// clamp before the indexed branch.
+#define BG_PTX_TBLPAD \
+    ", END_%=, END_%=, END_%=, END_%=, END_%=, END_%=, END_%=, END_%=, END_%=, END_%=, END_%="
 #define BG_PTX_DISPATCH                                                                    \
     "mov.b32 %8, %10;\n\tmov.b32 %9, %11;\n\t"                                             \
     "ld.shared.v2.u32 {%10, %11}, [%12];\n\t"                                              \
     "add.u32 %12, %12, 8;\n\t"                                                             \
     "and.b32 h, %8, 31;\n\t"                                                               \
-    "min.u32 h, h, 20;\n\t"                                                                \
     "brx.idx.uni h, TBL_%=;\n"
 #define BG_PTX_ROW "bfe.u32 v, %8, 12, 8;\n\tmad.lo.u32 rp, v, 512, %15;\n\t"
 #define BG_PTX_XA "bfe.u32 v, %8, 8, 4;\n\tmad.lo.u32 xa, v, 1024, %14;\n\t"
@@ -45,7 +50,7 @@ namespace beagle {
     ".reg .f32 a0, a1, a2, a3, s, z;\n\t"                                                  \
     "TBL_%=: .branchtargets PUSHX_%=, PUSHC_%=, DUP_%=, SWAP_%=, DEL_%=, ADDSUB_%=, "      \
     "MUL_%=, PDIV_%=, SIN_%=, COS_%=, EXP_%=, PLOG_%=, PSQRT_%=, SQUARE_%=, ADDSUBX_%=, "   \
-    "MULX_%=, PDIVX_%=, ADDC_%=, MULC_%=, PDIVC_%=, END_%=;\n\t"                           \
+    "MULX_%=, PDIVX_%=, ADDC_%=, MULC_%=, PDIVC_%=, END_%=" BG_PTX_TBLPAD ";\n\t"          \
     BG_PTX_DISPATCH                                                                        \
     "PUSHX_%=:\n\t" BG_PTX_ROW BG_PTX_XA                                                   \
     "st.shared.v4.f32 [rp], {%0, %1, %2, %3};\n\t"                                         \
@@ -88,7 +93,7 @@ namespace beagle {
     "PSQRT_%=:\n\t"                                                                        \
     "abs.f32 %0, %0;\n\tsqrt.rn.f32 %0, %0;\n\tabs.f32 %1, %1;\n\tsqrt.rn.f32 %1, %1;\n\t" \
     "abs.f32 %2, %2;\n\tsqrt.rn.f32 %2, %2;\n\tabs.f32 %3, %3;\n\tsqrt.rn.f32 %3, %3;\n\t" \
-    BG_PTX_TRACK4 BG_PTX_DISPATCH                                                          \
+    BG_PTX_DISPATCH                                                                        \
     "SQUARE_%=:\n\t"                                                                       \
     "mul.rn.f32 %0, %0, %0;\n\tmul.rn.f32 %1, %1, %1;\n\t"                                 \
     "mul.rn.f32 %2, %2, %2;\n\tmul.rn.f32 %3, %3, %3;\n\t"                                 \
@@ -154,6 +159,10 @@ __device__ __forceinline__ void run_program_ptx4(uint32_t prog, uint32_t xrow, u
         case H_EXP: t0 = A::exp_(t0); t1 = A::exp_(t1); t2 = A::exp_(t2); t3 = A::exp_(t3); break;
         default: t0 = A::plog(t0); t1 = A::plog(t1); t2 = A::plog(t2); t3 = A::plog(t3); break;
         }
+        // sin, cos and the protected log of a valid value are finite and bounded (|ln|v|| <=
+        // 69.1 for |v| <= 1e30), and an invalid operand was recorded when it was pushed, so
+        // only exp can produce a new invalid value here.
+        if (code != H_EXP) continue;
         m0 = A::track(m0, t0);
         m1 = A::track(m1, t1);
         m2 = A::track(m2, t2);
@@ -170,5 +179,6 @@ __device__ __forceinline__ void run_program_ptx4(uint32_t prog, uint32_t xrow, u
 #undef BG_PTX_ROW
 #undef BG_PTX_XA
 #undef BG_PTX_S
+#undef BG_PTX_TBLPAD
 
 }  // namespace beagle

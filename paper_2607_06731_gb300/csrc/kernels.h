@@ -36,5 +36,8 @@ void timing_end(cudaStream_t s, void *token);
 
 cudaError_t launch_score_batch(const LaunchParams<kMaxJobs> &prm, int precision, int cases,
                                int nw, int grid, cudaStream_t s);
+// Load every scoring and finalize kernel instantiation (module loading is lazy), so that a
+// later stream capture makes no loader calls.
+cudaError_t load_kernels();
 
 }  // namespace beagle

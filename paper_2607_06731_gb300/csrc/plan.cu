@@ -10,16 +10,6 @@
 
 namespace beagle {
 
-namespace {
-
-struct Planned {
-    JobDev dev;
-    const CUtensorMap *map;
-    size_t part_bytes;
-};
-
-size_t up256(size_t x) { return (x + 255) / 256 * 256; }
-
 // Keep freed stream-ordered scratch in the device's default pool instead of returning it to
 // the driver at every synchronisation, so repeated calls do not remap memory.
 void keep_pool_memory(int dev) {
@@ -34,6 +24,29 @@ void keep_pool_memory(int dev) {
     }
     done.push_back(dev);
 }
+
+beagle_status prepare_capture() {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    keep_pool_memory(dev);
+    const cudaError_t e = load_kernels();
+    return e == cudaSuccess ? BEAGLE_OK : cuda_fail(e, "loading the scoring kernels");
+}
+
+namespace {
+
+struct Planned {
+    JobDev dev;
+    const CUtensorMap *map;
+    size_t part_bytes;
+};
+
+size_t up256(size_t x) { return (x + 255) / 256 * 256; }
+
+// A launch is cut where the input rows change once it holds this many program-cases
+// (P x N summed over its jobs): about 10^9 node evaluations at typical program lengths, a
+// millisecond or more of GPU time, so the tail of a persistent launch is a small share.
+constexpr int64_t kLaunchCases = int64_t(1) << 24;
 
 template <int MAXJ>
 beagle_status enqueue(const std::vector<Planned> &jobs, size_t b, size_t e, int precision,
@@ -107,8 +120,6 @@ beagle_status score_jobs(const JobRequest *reqs, int n, int precision, cudaStrea
     keep_pool_memory(dev);
     std::vector<std::shared_ptr<Dataset>> keep;
     std::vector<Planned> jobs;
-    int max_rows = 1;
-    int64_t work = 0;
     for (int i = 0; i < n; ++i) {
         const JobRequest &r = reqs[i];
         if (r.P < 0) return fail(BEAGLE_ERR_ARG, "job %d: negative P", i);
@@ -137,65 +148,94 @@ beagle_status score_jobs(const JobRequest *reqs, int n, int precision, cudaStrea
         pj.dev.ybar = ds->ybar;
         pj.dev.syy = precision == BEAGLE_FP64 ? ds->syy : ds->syy32;
         pj.map = &ds->map;
-        max_rows = std::max(max_rows, ds->rows);
         keep.push_back(ds);
         jobs.push_back(pj);
     }
     if (jobs.empty()) return BEAGLE_OK;
 
-    // Launch shape: explicit tune, else the process-wide configuration, else the autotuner's
-    // entry for this shape class, else automatic: tile 512 cases, 4 cases per lane, as many
-    // consumer warps as shared memory allows, programs ordered by length.
-    Tune cfg = tune ? *tune : current_tune();
-    int64_t max_n = 1;
-    for (const auto &pj : jobs) max_n = std::max(max_n, pj.dev.N);
-    if (!tune && cfg.is_auto()) {
-        Tune t;
-        if (find_tuned(precision, max_rows, max_n, &t)) cfg = t;
+    // Launches: jobs in ascending order of input rows (d + 2), cut where the rows change once
+    // the launch holds enough work to fill the GPU, and at kMaxJobs jobs. A launch's shared
+    // memory is sized by its widest dataset, so mixing a narrow dataset into a wide launch
+    // would cost it consumer warps; tiny jobs still share launches.
+    std::vector<size_t> idx(jobs.size());
+    for (size_t i = 0; i < idx.size(); ++i) idx[i] = i;
+    std::stable_sort(idx.begin(), idx.end(),
+                     [&](size_t a, size_t b) { return jobs[a].dev.rows < jobs[b].dev.rows; });
+    const Tune cfg0 = tune ? *tune : current_tune();
+    std::vector<size_t> cur;
+    int64_t cur_cases = 0;   // sum of P x N of the launch being formed
+    auto flush = [&]() -> beagle_status {
+        if (cur.empty()) return BEAGLE_OK;
+        std::vector<Planned> lj;
+        std::vector<Dataset *> lds;
+        int rows = 1;
+        int64_t max_n = 1;
+        for (size_t i : cur) {
+            lj.push_back(jobs[i]);
+            lds.push_back(keep[i].get());
+            rows = std::max(rows, jobs[i].dev.rows);
+            max_n = std::max(max_n, jobs[i].dev.N);
+        }
+        cur.clear();
+        cur_cases = 0;
+        // Launch shape: explicit tune, else the process-wide configuration, else the
+        // autotuner's entry for this shape class, else automatic: tile 512 cases, 4 cases per
+        // lane, as many consumer warps as shared memory allows, programs ordered by length.
+        Tune cfg = cfg0;
+        if (!tune && cfg.is_auto()) {
+            Tune t;
+            if (find_tuned(precision, rows, max_n, &t)) cfg = t;
+        }
+        int tile = 512;
+        if (cfg.tile) {
+            if (cfg.tile != 512 && cfg.tile != 1024)
+                return fail(BEAGLE_ERR_ARG, "tile must be 512 or 1024");
+            tile = cfg.tile;
+        }
+        int cases = kCasesFp32;
+        if (cfg.cases) {
+            if (cfg.cases != 2 && cfg.cases != 4 && cfg.cases != 8)
+                return fail(BEAGLE_ERR_ARG, "cases per lane must be 2, 4 or 8");
+            cases = cfg.cases;
+        }
+        const int xbuf_floats = rows * tile;
+        const int grid = cfg.grid ? cfg.grid : sm_count();
+        int nw = plan_warps(precision, cases, xbuf_floats, tile);
+        if (cfg.warps) nw = std::min(nw, cfg.warps);
+        if (nw < 1 || smem_bytes(precision, cases, xbuf_floats, tile, nw) > kSmemBudget)
+            return fail(BEAGLE_ERR_LIMIT, "shared memory plan exceeds %zu bytes", kSmemBudget);
+        const int which = tile == 512 ? 0 : 1;
+        int64_t work = 0;
+        for (size_t i = 0; i < lj.size(); ++i) {
+            JobDev &J = lj[i].dev;
+            J.tiles = static_cast<int32_t>((J.N + tile - 1) / tile);
+            J.tile_sy = precision == BEAGLE_FP64 ? lds[i]->tile_sy64[which] : lds[i]->tile_sy[which];
+            lj[i].part_bytes = static_cast<size_t>(kNumFields) * J.tiles * J.P * sizeof(uint32_t);
+            work += J.P * J.tiles;
+        }
+        // Programs per work item: about 32 items per CTA, at least two per consumer warp (a
+        // smaller item leaves warps waiting for the next staged tile) and at most 256.
+        int group = static_cast<int>(
+            std::min<int64_t>(256, std::max<int64_t>(2 * nw, work / (32LL * grid))));
+        if (cfg.group) group = cfg.group;
+        const bool sort = !cfg.unsorted;
+        if (lj.size() == 1)
+            return enqueue<1>(lj, 0, 1, precision, cases, tile, group, nw, grid, xbuf_floats,
+                              sort, s);
+        return enqueue<kMaxJobs>(lj, 0, lj.size(), precision, cases, tile, group, nw, grid,
+                                 xbuf_floats, sort, s);
+    };
+    for (size_t i : idx) {
+        if (!cur.empty() && (cur.size() == static_cast<size_t>(kMaxJobs) ||
+                             (jobs[i].dev.rows != jobs[cur.back()].dev.rows &&
+                              cur_cases >= kLaunchCases))) {
+            const beagle_status st = flush();
+            if (st != BEAGLE_OK) return st;
+        }
+        cur.push_back(i);
+        cur_cases += jobs[i].dev.P * jobs[i].dev.N;
     }
-    int tile = 512;
-    if (cfg.tile) {
-        if (cfg.tile != 512 && cfg.tile != 1024)
-            return fail(BEAGLE_ERR_ARG, "tile must be 512 or 1024");
-        tile = cfg.tile;
-    }
-    int cases = kCasesFp32;
-    if (cfg.cases) {
-        if (cfg.cases != 2 && cfg.cases != 4 && cfg.cases != 8)
-            return fail(BEAGLE_ERR_ARG, "cases per lane must be 2, 4 or 8");
-        cases = cfg.cases;
-    }
-    const int xbuf_floats = max_rows * tile;
-    int grid = cfg.grid ? cfg.grid : sm_count();
-    int nw = plan_warps(precision, cases, xbuf_floats, tile);
-    if (cfg.warps) nw = std::min(nw, cfg.warps);
-    if (nw < 1 || smem_bytes(precision, cases, xbuf_floats, tile, nw) > kSmemBudget)
-        return fail(BEAGLE_ERR_LIMIT, "shared memory plan exceeds %zu bytes", kSmemBudget);
-    const int which = tile == 512 ? 0 : 1;
-    for (size_t i = 0; i < jobs.size(); ++i) {
-        JobDev &J = jobs[i].dev;
-        J.tiles = static_cast<int32_t>((J.N + tile - 1) / tile);
-        J.tile_sy = precision == BEAGLE_FP64 ? keep[i]->tile_sy64[which] : keep[i]->tile_sy[which];
-        jobs[i].part_bytes = static_cast<size_t>(kNumFields) * J.tiles * J.P * sizeof(uint32_t);
-        work += J.P * J.tiles;
-    }
-    // Programs per work item: about 32 items per CTA, at least two per consumer warp (a
-    // smaller item leaves warps waiting for the next staged tile) and at most 256.
-    int group = static_cast<int>(
-        std::min<int64_t>(256, std::max<int64_t>(2 * nw, work / (32LL * grid))));
-    if (cfg.group) group = cfg.group;
-
-    const bool sort = !cfg.unsorted;
-    if (jobs.size() == 1)
-        return enqueue<1>(jobs, 0, 1, precision, cases, tile, group, nw, grid, xbuf_floats,
-                          sort, s);
-    for (size_t b = 0; b < jobs.size(); b += kMaxJobs) {
-        const size_t e = std::min(jobs.size(), b + kMaxJobs);
-        beagle_status st = enqueue<kMaxJobs>(jobs, b, e, precision, cases, tile, group, nw,
-                                             grid, xbuf_floats, sort, s);
-        if (st != BEAGLE_OK) return st;
-    }
-    return BEAGLE_OK;
+    return flush();
 }
 
 static std::mutex g_tune_mu;

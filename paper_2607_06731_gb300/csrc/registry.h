@@ -69,6 +69,11 @@ bool find_tuned(int precision, int rows, int64_t max_n, Tune *out);
 void store_tuned(int precision, int rows, int64_t max_n, const Tune &t);
 void clear_tuned();
 
+// Everything a stream capture of score_jobs must not do the first time: set the memory pool's
+// release threshold and load the kernels. Called before capturing.
+void keep_pool_memory(int dev);
+beagle_status prepare_capture();
+
 // Enqueue scoring of n jobs on stream s (one persistent launch per 64 jobs).
 beagle_status score_jobs(const JobRequest *reqs, int n, int precision, cudaStream_t s,
                          const Tune *tune);

@@ -444,6 +444,24 @@ static cudaError_t launch_any(const LaunchParams<MAXJ> &prm, int precision, int 
     }
 }
 
+template <typename T, int K, int MAXJ>
+static cudaError_t load_one() {
+    cudaFuncAttributes a;
+    cudaError_t e = cudaFuncGetAttributes(&a, score_kernel<T, K, kMaxDepth, MAXJ>);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, finalize_kernel<sizeof(T) == 8, MAXJ>);
+    return e;
+}
+
+cudaError_t load_kernels() {
+    cudaError_t e = cudaSuccess;
+    for (cudaError_t r : {load_one<float, 2, 1>(), load_one<float, 4, 1>(), load_one<float, 8, 1>(),
+                          load_one<double, kCasesFp64, 1>(), load_one<float, 2, kMaxJobs>(),
+                          load_one<float, 4, kMaxJobs>(), load_one<float, 8, kMaxJobs>(),
+                          load_one<double, kCasesFp64, kMaxJobs>()})
+        if (r != cudaSuccess) e = r;
+    return e;
+}
+
 cudaError_t launch_score(const LaunchParams<1> &prm, int precision, int cases, int nw, int grid,
                          cudaStream_t s) {
     return launch_any<1>(prm, precision, cases, nw, grid, s);

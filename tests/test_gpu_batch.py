@@ -122,3 +122,35 @@ def test_launch_configurations_agree():
     finally:
         beagle.reset_launch_config()
     ds.release()
+
+
+def test_plan_capture_as_the_first_call_of_a_process():
+    """A graph-captured plan built before any other scoring call in a fresh process (pool
+    set-up and kernel loading happen before the capture begins)."""
+    import subprocess
+    import sys
+    import textwrap
+    code = textwrap.dedent("""
+        import numpy as np, torch
+        from paper_2607_06731_gb300 import beagle, synth as S
+        pops = S.make_c4(seed=11, n_pops=5, scale=0.01)
+        items = []
+        for pr in pops:
+            items.append((beagle.DevicePrograms(pr.programs), beagle.Dataset(pr.X, pr.y),
+                          torch.full((pr.programs.P, 3), float("nan"), dtype=torch.float64,
+                                     device="cuda")))
+        plan = beagle.BatchPlan(items)
+        plan.launch()
+        torch.cuda.synchronize()
+        for dp, ds, out in items:
+            ref = beagle.unpack_fitness(beagle.score_programs(dp, ds))
+            got = beagle.unpack_fitness(out)
+            torch.cuda.synchronize()
+            assert all(np.array_equal(a, b, equal_nan=True) for a, b in zip(got, ref))
+        print("ok")
+    """)
+    import os
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, "-c", code], cwd=root, capture_output=True, text=True,
+                       timeout=600)
+    assert r.returncode == 0 and r.stdout.strip().endswith("ok"), r.stderr[-2000:]

@@ -139,7 +139,7 @@ def test_oversize_request_fails_alone():
 
 
 def test_wait_timeout_keeps_the_ticket_and_poll_collects():
-    pr = S.make_c2(seed=2, scale=0.2)          # a few ms of work
+    pr = S.make_c2(seed=2, P=20_000)           # a few ms of work
     ds = beagle.Dataset(pr.X, pr.y)
     srv = beagle.Server()
     t = srv.submit(pr.programs, ds)
