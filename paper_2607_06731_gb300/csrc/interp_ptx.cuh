@@ -6,7 +6,7 @@
 // skips the protected square root, sin, cos and the protected log, whose results are finite
 // and at most 1e15 in magnitude whenever their operand is valid). sin, cos, exp and
 // the protected log leave the loop with their handler id; the caller applies them to the top
-// of stack (CUDA's sinf, cosf, expf, logf) and re-enters.
+// of stack (transcend.cuh's branch-free sin, cos and log; CUDA's expf) and re-enters.
 #pragma once
 
 #include "score.cuh"
@@ -154,8 +154,8 @@ __device__ __forceinline__ void run_program_ptx4(uint32_t prog, uint32_t xrow, u
                      : "memory");
         if (code == 0) break;
         switch (code) {
-        case H_SIN: t0 = A::sin_(t0); t1 = A::sin_(t1); t2 = A::sin_(t2); t3 = A::sin_(t3); break;
-        case H_COS: t0 = A::cos_(t0); t1 = A::cos_(t1); t2 = A::cos_(t2); t3 = A::cos_(t3); break;
+        case H_SIN:
+        case H_COS: sincos4(t0, t1, t2, t3, static_cast<int>(code) - H_SIN); break;
         case H_EXP: t0 = A::exp_(t0); t1 = A::exp_(t1); t2 = A::exp_(t2); t3 = A::exp_(t3); break;
         default: t0 = A::plog(t0); t1 = A::plog(t1); t2 = A::plog(t2); t3 = A::plog(t3); break;
         }

@@ -1,0 +1,103 @@
+// sin, cos and the protected log of the FP32 path (exp is CUDA's expf).
+//
+// The interpreter applies each of these to the 4 cases of a lane at once. CUDA's sinf, cosf
+// and logf are written for one argument (sinf and cosf branch per call to a slow path for
+// large arguments), so four calls run one after another. The forms here are branch-free in
+// the common case, so the four evaluations interleave, and sin and cos share one body
+// (CUDA's expf, built on the hardware exponential, stays faster than a polynomial form):
+//
+//   sin, cos  Cody and Waite's additive range reduction k = rint(x 2/pi), r = x - k pi/2 with
+//             pi/2 held as three fp32 parts (fused multiply-adds; the first step is exact since
+//             x and k C1 share their low bits), |r| <= pi/4 (1 % more when the rounded quotient
+//             is off by one). Quadrant q = k for sin and k + 1 for cos (cos x = sin(x + pi/2));
+//             odd q takes the cosine polynomial and q & 2 flips the sign. sin r = r + r^3 P(s),
+//             cos r = 1 + s Q(s), s = r^2. Arguments above 65536 in magnitude (and NaN) take
+//             CUDA's sinf/cosf on the lanes that hold them.
+//   plog      ln|x| for |x| > 1e-3, else 0: |x| = m 2^e with m in [sqrt(1/2), sqrt(2)),
+//             ln m = f + f^2 (-1/2 + f L(f)), f = m - 1 (exact), plus e ln 2 in two parts.
+//             Only valid operands matter (finite, |x| <= 1e30): the results for others are
+//             never used, because the program is already invalid.
+//
+// P, Q and L are polynomials whose coefficients gen_poly.py (beside this file) fits to
+// relative error and rounds to fp32; with exact evaluation their maximum relative errors are
+// 3.6e-9, 3.9e-9 and 6.6e-9 (under 0.1 ulp). Each result is a function of its argument alone,
+// so every path and launch shape gives the same bits.
+#pragma once
+
+namespace beagle {
+
+constexpr float kTwoOverPi = 0x1.45f306p-1f;
+constexpr float kPio2C1 = 0x1.921fb6p+0f;
+constexpr float kPio2C2 = -0x1.777a5cp-25f;
+constexpr float kPio2C3 = -0x1.ee59dap-50f;
+constexpr float kSinP0 = -0x1.555556p-3f, kSinP1 = 0x1.111108p-7f, kSinP2 = -0x1.a00f12p-13f,
+                kSinP3 = 0x1.6cb80cp-19f;
+constexpr float kCosQ0 = -0x1.0p-1f, kCosQ1 = 0x1.55553ap-5f, kCosQ2 = -0x1.6c0756p-10f,
+                kCosQ3 = 0x1.98f230p-16f;
+constexpr float kSinCosFastLimit = 65536.0f;
+
+constexpr float kLn2Hi = 0x1.62e430p-1f;
+constexpr float kLn2Lo = -0x1.05c610p-29f;
+constexpr float kLogL0 = 0x1.555554p-2f, kLogL1 = -0x1.000226p-2f, kLogL2 = 0x1.99a01ep-3f,
+                kLogL3 = -0x1.547254p-3f, kLogL4 = 0x1.22d8aep-3f, kLogL5 = -0x1.0d837cp-3f,
+                kLogL6 = 0x1.0562e0p-3f, kLogL7 = -0x1.38ceaap-4f;
+constexpr float kLogTiny = 1e-3f;
+
+// ---------------------------------------------------------------- sin, cos (qo = 0 / 1)
+__device__ __forceinline__ float sincos_fast(float x, int qo) {
+    const float kf = rintf(x * kTwoOverPi);
+    float r = fmaf(-kf, kPio2C1, x);
+    r = fmaf(-kf, kPio2C2, r);
+    r = fmaf(-kf, kPio2C3, r);
+    const int q = __float2int_rn(kf) + qo;
+    const float s = r * r;
+    const bool odd = (q & 1) != 0;
+    const float c3 = odd ? kCosQ3 : kSinP3;
+    const float c2 = odd ? kCosQ2 : kSinP2;
+    const float c1 = odd ? kCosQ1 : kSinP1;
+    const float c0 = odd ? kCosQ0 : kSinP0;
+    const float p = fmaf(fmaf(fmaf(c3, s, c2), s, c1), s, c0);
+    const float base = odd ? 1.0f : r;
+    const float v = fmaf(base * s, p, base);
+    return (q & 2) ? -v : v;
+}
+
+__device__ __forceinline__ float sincos_dev(float x, int qo) {
+    if (fabsf(x) <= kSinCosFastLimit) return sincos_fast(x, qo);
+    return qo ? cosf(x) : sinf(x);
+}
+
+__device__ __forceinline__ void sincos4(float &t0, float &t1, float &t2, float &t3, int qo) {
+    const float a0 = t0, a1 = t1, a2 = t2, a3 = t3;
+    t0 = sincos_fast(a0, qo);
+    t1 = sincos_fast(a1, qo);
+    t2 = sincos_fast(a2, qo);
+    t3 = sincos_fast(a3, qo);
+    const float big = fmaxf(fmaxf(fabsf(a0), fabsf(a1)), fmaxf(fabsf(a2), fabsf(a3)));
+    if (!(big <= kSinCosFastLimit)) {
+        if (!(fabsf(a0) <= kSinCosFastLimit)) t0 = qo ? cosf(a0) : sinf(a0);
+        if (!(fabsf(a1) <= kSinCosFastLimit)) t1 = qo ? cosf(a1) : sinf(a1);
+        if (!(fabsf(a2) <= kSinCosFastLimit)) t2 = qo ? cosf(a2) : sinf(a2);
+        if (!(fabsf(a3) <= kSinCosFastLimit)) t3 = qo ? cosf(a3) : sinf(a3);
+    }
+}
+
+// ---------------------------------------------------------------- protected log
+__device__ __forceinline__ float plog_dev(float x) {
+    const float a = fabsf(x);
+    int bits = __float_as_int(a);
+    int e = (bits >> 23) - 127;
+    int mb = (bits & 0x007fffff) | 0x3f800000;
+    const bool hi = mb > 0x3fb504f3;            // m > sqrt(2): take m / 2
+    mb = hi ? mb - 0x00800000 : mb;
+    e = hi ? e + 1 : e;
+    const float f = __int_as_float(mb) - 1.0f;
+    float l = fmaf(fmaf(fmaf(kLogL7, f, kLogL6), f, kLogL5), f, kLogL4);
+    l = fmaf(fmaf(fmaf(fmaf(l, f, kLogL3), f, kLogL2), f, kLogL1), f, kLogL0);
+    const float lnm = fmaf(f * f, fmaf(f, l, -0.5f), f);
+    const float ef = static_cast<float>(e);
+    const float v = fmaf(ef, kLn2Hi, fmaf(ef, kLn2Lo, lnm));
+    return a > kLogTiny ? v : 0.0f;
+}
+
+}  // namespace beagle
