@@ -6,7 +6,7 @@
 // the common case, so the four evaluations interleave, and sin and cos share one body
 // (CUDA's expf, built on the hardware exponential, stays faster than a polynomial form):
 //
-//   sin, cos  Cody and Waite's additive range reduction k = rint(x 2/pi), r = x - k pi/2 with
+//   sin, cos  Cody and Waite's additive range reduction k = round(x 2/pi), r = x - k pi/2 with
 //             pi/2 held as three fp32 parts (fused multiply-adds; the first step is exact since
 //             x and k C1 share their low bits), |r| <= pi/4 (1 % more when the rounded quotient
 //             is off by one). Quadrant q = k for sin and k + 1 for cos (cos x = sin(x + pi/2));
@@ -44,12 +44,18 @@ constexpr float kLogL0 = 0x1.555554p-2f, kLogL1 = -0x1.000226p-2f, kLogL2 = 0x1.
 constexpr float kLogTiny = 1e-3f;
 
 // ---------------------------------------------------------------- sin, cos (qo = 0 / 1)
+// Adding 1.5 * 2^23 rounds a float of magnitude below 2^22 to an integer held in the low
+// mantissa bits: the rounding and the conversion to int without the conversion unit.
+constexpr float kRoundMagic = 0x1.8p+23f;
+constexpr int kRoundMagicBits = 0x4b400000;
+
 __device__ __forceinline__ float sincos_fast(float x, int qo) {
-    const float kf = rintf(x * kTwoOverPi);
+    const float t = fmaf(x, kTwoOverPi, kRoundMagic);   // |x 2/pi| < 2^22 on this path
+    const float kf = t - kRoundMagic;                    // k = x 2/pi rounded to nearest
     float r = fmaf(-kf, kPio2C1, x);
     r = fmaf(-kf, kPio2C2, r);
     r = fmaf(-kf, kPio2C3, r);
-    const int q = __float2int_rn(kf) + qo;
+    const int q = (__float_as_int(t) - kRoundMagicBits) + qo;
     const float s = r * r;
     const bool odd = (q & 1) != 0;
     const float c3 = odd ? kCosQ3 : kSinP3;
@@ -62,9 +68,13 @@ __device__ __forceinline__ float sincos_fast(float x, int qo) {
     return (q & 2) ? -v : v;
 }
 
+// Large arguments: one out-of-line copy of CUDA's functions, so that their long reduction
+// code stays out of the interpreter's instruction stream.
+static __device__ __noinline__ float sincos_slow(float x, int qo) { return qo ? cosf(x) : sinf(x); }
+
 __device__ __forceinline__ float sincos_dev(float x, int qo) {
     if (fabsf(x) <= kSinCosFastLimit) return sincos_fast(x, qo);
-    return qo ? cosf(x) : sinf(x);
+    return sincos_slow(x, qo);
 }
 
 __device__ __forceinline__ void sincos4(float &t0, float &t1, float &t2, float &t3, int qo) {
@@ -75,10 +85,10 @@ __device__ __forceinline__ void sincos4(float &t0, float &t1, float &t2, float &
     t3 = sincos_fast(a3, qo);
     const float big = fmaxf(fmaxf(fabsf(a0), fabsf(a1)), fmaxf(fabsf(a2), fabsf(a3)));
     if (!(big <= kSinCosFastLimit)) {
-        if (!(fabsf(a0) <= kSinCosFastLimit)) t0 = qo ? cosf(a0) : sinf(a0);
-        if (!(fabsf(a1) <= kSinCosFastLimit)) t1 = qo ? cosf(a1) : sinf(a1);
-        if (!(fabsf(a2) <= kSinCosFastLimit)) t2 = qo ? cosf(a2) : sinf(a2);
-        if (!(fabsf(a3) <= kSinCosFastLimit)) t3 = qo ? cosf(a3) : sinf(a3);
+        if (!(fabsf(a0) <= kSinCosFastLimit)) t0 = sincos_slow(a0, qo);
+        if (!(fabsf(a1) <= kSinCosFastLimit)) t1 = sincos_slow(a1, qo);
+        if (!(fabsf(a2) <= kSinCosFastLimit)) t2 = sincos_slow(a2, qo);
+        if (!(fabsf(a3) <= kSinCosFastLimit)) t3 = sincos_slow(a3, qo);
     }
 }
 
@@ -95,7 +105,7 @@ __device__ __forceinline__ float plog_dev(float x) {
     float l = fmaf(fmaf(fmaf(kLogL7, f, kLogL6), f, kLogL5), f, kLogL4);
     l = fmaf(fmaf(fmaf(fmaf(l, f, kLogL3), f, kLogL2), f, kLogL1), f, kLogL0);
     const float lnm = fmaf(f * f, fmaf(f, l, -0.5f), f);
-    const float ef = static_cast<float>(e);
+    const float ef = __int_as_float(kRoundMagicBits + e) - kRoundMagic;   // exact for |e| < 2^22
     const float v = fmaf(ef, kLn2Hi, fmaf(ef, kLn2Lo, lnm));
     return a > kLogTiny ? v : 0.0f;
 }
