@@ -113,6 +113,30 @@ class Clocks:
                 "samples": len(sm)}
 
 
+# DRAM traffic of the scoring kernel from an ncu capture (dram__bytes_read.sum +
+# dram__bytes_write.sum of the P = 20,000 case, scaled by 5 to a full launch: traffic is per
+# program), valid only for the kernel sources it was taken on (profiles/ has the capture).
+TRAFFIC_CAPTURE = {"sources_sha256": None, "bytes_per_launch": None}
+
+
+def kernel_sources_sha256():
+    import hashlib
+    d = os.path.join(ROOT, "paper_2607_06731_gb300", "csrc")
+    h = hashlib.sha256()
+    for name in sorted(os.listdir(d)):
+        if name.endswith((".cu", ".cuh", ".h")):
+            h.update(name.encode())
+            h.update(open(os.path.join(d, name), "rb").read())
+    return h.hexdigest()
+
+
+def captured_traffic():
+    cap = TRAFFIC_CAPTURE
+    if cap["sources_sha256"] and cap["sources_sha256"] == kernel_sources_sha256():
+        return cap["bytes_per_launch"]
+    return None
+
+
 def roofline_peak(progs, N, rates):
     """ALU-issue roofline: the time straight-line compiled code would need for this op mix,
     every operator at its measured throughput (validity check included), leaves free."""
@@ -561,7 +585,8 @@ def main():
             "frac_within_1e-5": float(within.mean()) if ok.any() else None,
             "median_rel": float(np.median(rel)) if ok.any() else None},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "GPoPs",
-                     "frac": achieved / peak, "traffic": None,
+                     "frac": achieved / peak, "traffic": captured_traffic(),
+                     "traffic_unit": "bytes per launch (ncu dram read + write)",
                      "peak_basis": "per-op throughput measured by beagle_measure_op_rates "
                                    "on this GPU (validity check included, leaves free)",
                      "kernel_ms": kern_avg_s * 1e3},

@@ -33,11 +33,13 @@ namespace beagle {
 // clamp before the indexed branch.
 #define BG_PTX_TBLPAD \
     ", END_%=, END_%=, END_%=, END_%=, END_%=, END_%=, END_%=, END_%=, END_%=, END_%=, END_%="
+// The handler index is taken from the prefetched token first, so the indexed branch does not
+// wait on the instruction just before it.
 #define BG_PTX_DISPATCH                                                                    \
+    "and.b32 h, %10, 31;\n\t"                                                              \
     "mov.b32 %8, %10;\n\tmov.b32 %9, %11;\n\t"                                             \
     "ld.shared.v2.u32 {%10, %11}, [%12];\n\t"                                              \
     "add.u32 %12, %12, 8;\n\t"                                                             \
-    "and.b32 h, %8, 31;\n\t"                                                               \
     "brx.idx.uni h, TBL_%=;\n"
 #define BG_PTX_ROW "bfe.u32 v, %8, 12, 8;\n\tmad.lo.u32 rp, v, 512, %15;\n\t"
 #define BG_PTX_XA "bfe.u32 v, %8, 8, 4;\n\tmad.lo.u32 xa, v, 1024, %14;\n\t"

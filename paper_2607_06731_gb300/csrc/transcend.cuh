@@ -34,7 +34,7 @@ constexpr float kSinP0 = -0x1.555556p-3f, kSinP1 = 0x1.111108p-7f, kSinP2 = -0x1
                 kSinP3 = 0x1.6cb80cp-19f;
 constexpr float kCosQ0 = -0x1.0p-1f, kCosQ1 = 0x1.55553ap-5f, kCosQ2 = -0x1.6c0756p-10f,
                 kCosQ3 = 0x1.98f230p-16f;
-constexpr float kSinCosFastLimit = 65536.0f;
+constexpr float kSinCosFastLimit = 0x1.0p+16f;   // 65536
 
 constexpr float kLn2Hi = 0x1.62e430p-1f;
 constexpr float kLn2Lo = -0x1.05c610p-29f;
