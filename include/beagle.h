@@ -9,7 +9,7 @@
  *     fitness per program; the CPU keeps the genetic operators (Section 2.4). Genomes go to
  *     the device once per generation and datasets stay resident (Sections 2.4, 3.6).
  *   - Fitness is the mean squared error and 1 - r^2, r being the Pearson correlation of
- *     Eq. 1 between outputs and targets ("The r value is then squared", Section 2.10).
+ *     Eq. 1 between outputs and targets, squared (Section 2.10).
  *
  * Readings of points the paper leaves open (the paper's own DIV, LN, SQRT are unprotected):
  *   pdiv(a, b) = a / b if |b| > 1e-3, else 1;  plog(a) = ln|a| if |a| > 1e-3, else 0;

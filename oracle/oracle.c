@@ -13,7 +13,7 @@
  *   - Each program runs on every fitness case and one aggregated fitness per program is
  *     returned (Section 2.4).
  *   - Fitness: mean squared error, and 1 - r^2 with r the Pearson correlation of Eq. 1
- *     (Section 2.10, "The r value is then squared").
+ *     (Section 2.10: the paper squares r).
  * Readings where the paper is silent (protected operators, the validity rule, the
  * degenerate-r rule) are stated where they are used below.
  *
