@@ -246,7 +246,8 @@ beagle_status beagle_serve_destroy(beagle_server *server);
 /*
  * Launch shape of the scoring kernel (no counterpart in the paper). All fields 0 = chosen
  * automatically. cases_per_lane: fitness cases each lane evaluates per pass on the FP32 path
- * (2, 4 or 8); tile: cases per staged tile (512 or 1024); group: programs per work item;
+ * (2, 4 or 8); tile: cases per staged tile (256 or 512; 8 cases per lane always uses 256);
+ * group: programs per work item;
  * warps: upper bound on consumer warps per CTA (1-31); grid: CTAs (default one per SM);
  * keep_order: 1 processes programs in the caller's order, 0 in the length-bucketed order
  * (longest first) where the planner chooses it.
@@ -320,7 +321,7 @@ beagle_status beagle_batch_plan_launch(beagle_batch_plan *plan, void *stream);
 beagle_status beagle_batch_plan_destroy(beagle_batch_plan *plan);
 
 /*
- * Autotuner: time candidate launch shapes (cases per lane 2/4/8 x tile 512/1024 x programs per
+ * Autotuner: time candidate launch shapes (cases per lane 2/4/8 x tile 512/256 x programs per
  * item) on the given jobs (it runs them, overwriting fitness_out) and remember the fastest for
  * this shape class (precision, d, floor(log2 of the largest N)); later calls of that class
  * with an automatic configuration use it. max_trials <= 0 tries all candidates. Synchronous.

@@ -125,7 +125,7 @@ beagle_status beagle_autotune(const beagle_job *jobs, int32_t n_jobs, int32_t pr
     // Candidates: cases per lane x tile x programs per item (0 = planner's choice).
     std::vector<Tune> cand;
     const int cases_list[3] = {4, 2, 8};
-    const int tile_list[2] = {512, 1024};
+    const int tile_list[2] = {512, 256};
     const int group_list[2] = {0, 64};
     for (int c : cases_list)
         for (int t : tile_list)

@@ -7,6 +7,13 @@ namespace beagle {
 
 constexpr int kMaxThreads = 1024;          // 31 consumer warps + 1 producer warp at most
 constexpr int kCasesFp32 = 4;              // default fitness cases per lane, FP32 path (2, 4, 8)
+
+// Cases per tile for a launch shape: the 8-case FP32 path runs one 256-case tile per pass;
+// the others default to 512.
+inline int tile_for(int precision, int cases, int requested) {
+    if (precision == BEAGLE_FP32_COMPENSATED && cases == 8) return 256;
+    return requested ? requested : 512;
+}
 constexpr int kCasesFp64 = 2;              // fitness cases per lane per pass, FP64 path
 constexpr size_t kSmemBudget = 227 * 1024; // dynamic shared memory per CTA
 

@@ -186,18 +186,15 @@ beagle_status score_jobs(const JobRequest *reqs, int n, int precision, cudaStrea
             Tune t;
             if (find_tuned(precision, rows, max_n, &t)) cfg = t;
         }
-        int tile = 512;
-        if (cfg.tile) {
-            if (cfg.tile != 512 && cfg.tile != 1024)
-                return fail(BEAGLE_ERR_ARG, "tile must be 512 or 1024");
-            tile = cfg.tile;
-        }
+        if (cfg.tile && cfg.tile != 512 && cfg.tile != 256)
+            return fail(BEAGLE_ERR_ARG, "tile must be 256 or 512");
         int cases = kCasesFp32;
         if (cfg.cases) {
             if (cfg.cases != 2 && cfg.cases != 4 && cfg.cases != 8)
                 return fail(BEAGLE_ERR_ARG, "cases per lane must be 2, 4 or 8");
             cases = cfg.cases;
         }
+        const int tile = tile_for(precision, cases, cfg.tile);
         const int xbuf_floats = rows * tile;
         const int grid = cfg.grid ? cfg.grid : sm_count();
         int nw = plan_warps(precision, cases, xbuf_floats, tile);
@@ -293,8 +290,8 @@ extern "C" beagle_status beagle_set_launch_config(const beagle_launch_config *cf
         if (cfg->cases_per_lane && cfg->cases_per_lane != 2 && cfg->cases_per_lane != 4 &&
             cfg->cases_per_lane != 8)
             return beagle::fail(BEAGLE_ERR_ARG, "cases_per_lane must be 0, 2, 4 or 8");
-        if (cfg->tile && cfg->tile != 512 && cfg->tile != 1024)
-            return beagle::fail(BEAGLE_ERR_ARG, "tile must be 0, 512 or 1024");
+        if (cfg->tile && cfg->tile != 512 && cfg->tile != 256)
+            return beagle::fail(BEAGLE_ERR_ARG, "tile must be 0, 256 or 512");
         if (cfg->warps < 0 || cfg->warps > 31 || cfg->group < 0 || cfg->grid < 0)
             return beagle::fail(BEAGLE_ERR_ARG, "bad launch configuration");
         t.cases = cfg->cases_per_lane;

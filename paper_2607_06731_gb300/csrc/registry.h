@@ -7,7 +7,7 @@
 
 namespace beagle {
 
-constexpr int kTileSizes[2] = {512, 1024};   // cases per tile the kernels support
+constexpr int kTileSizes[2] = {512, 256};    // cases per tile the kernels support
 
 // A resident dataset: rows x_0..x_{d-1}, y, y - ybar, each padded to npad floats.
 struct Dataset {

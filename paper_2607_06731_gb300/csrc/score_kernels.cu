@@ -2,6 +2,7 @@
 #include <cstdio>
 
 #include "interp_ptx.cuh"
+#include "interp_ptx8.cuh"
 #include "kernels.h"
 #include "score.cuh"
 
@@ -11,7 +12,7 @@ namespace beagle {
 //   [0, 64)        mbarriers: full[2], empty[2]
 //   [64, 128)      slot descriptors (2 x Slot)
 //   [128, ...)     X stage buffers: 2 x xbuf_floats fp32 (TMA destinations, 128-byte aligned)
-//   ...            per-warp output buffers: nw x tile x T
+//   ...            per-warp output buffers: nw x tile x T (none on the 8-case FP32 path)
 //   ...            per-warp packed programs: nw x (kMaxLen + 2) x uint2
 //   ...            per-warp value stacks: nw x (kMaxDepth - 1) rows x 32 K x T
 struct Slot {
@@ -29,7 +30,8 @@ struct SmemLayout {
         return xbuf_off() + 2ull * xbuf_floats * sizeof(float);
     }
     static __host__ __device__ size_t pbuf_off(int xbuf_floats, int tile, int nw) {
-        return fbuf_off(xbuf_floats) + static_cast<size_t>(nw) * tile * sizeof(T);
+        return fbuf_off(xbuf_floats) +
+               (sizeof(T) == 4 && K == 8 ? 0 : static_cast<size_t>(nw) * tile * sizeof(T));
     }
     static __host__ __device__ size_t stack_off(int xbuf_floats, int tile, int nw) {
         return pbuf_off(xbuf_floats, tile, nw) + static_cast<size_t>(nw) * (kMaxLen + 2) * sizeof(uint2);
@@ -42,11 +44,61 @@ struct SmemLayout {
     }
 };
 
+// The 8-case FP32 path runs one 256-case tile per pass and keeps the outputs in registers;
+// the other paths write them to the warp's shared-memory buffer.
+template <typename T, int K>
+constexpr bool kOutputsInRegs = sizeof(T) == 4 && K == 8;
+
+// A tile's outputs in the order the statistics read them: lane l's values are the cases
+// 128 h + 4 l + j (h over the tile's 128-case halves, j = 0..3), the order in which the 8-case
+// path holds them, so every path forms the same sums in the same order.
+template <typename T, int K>
+struct TileValues {
+    T r[kOutputsInRegs<T, K> ? 8 : 1];
+    const T *buf;
+    // values 4h..4h+3 of this lane (h a compile-time index on the register path)
+    __device__ __forceinline__ void get4(int h, int lane, T (&v)[4]) const {
+        if constexpr (kOutputsInRegs<T, K>) {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) v[j] = r[4 * h + j];
+        } else if constexpr (sizeof(T) == 4) {
+            const float4 q = *reinterpret_cast<const float4 *>(buf + h * 128 + lane * 4);
+            v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+        } else {
+            const double2 *src = reinterpret_cast<const double2 *>(buf + h * 128 + lane * 4);
+            const double2 a = src[0], b = src[1];
+            v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+        }
+    }
+    // f(h, v) for every 128-case half of the tile that holds cases
+    template <typename F>
+    __device__ __forceinline__ void for_halves(int halves, int lane, F &&f) const {
+        if constexpr (kOutputsInRegs<T, K>) {
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                if (h < halves) {
+                    T v[4];
+                    get4(h, lane, v);
+                    f(h, v);
+                }
+            }
+        } else {
+#pragma unroll 1
+            for (int h = 0; h < halves; ++h) {
+                T v[4];
+                get4(h, lane, v);
+                f(h, v);
+            }
+        }
+    }
+};
+
 template <typename T, int K, int D>
 __device__ __forceinline__ void process_program(const JobDev &J, int64_t p, int t, int tile,
                                                 const float *xs, uint2 *pbuf, T *fbuf, T *stk,
                                                 int lane) {
     using Sum = typename SumOf<T>::type;
+    constexpr bool kRegs = kOutputsInRegs<T, K>;
     constexpr int CH = 32 * K;
     const int64_t off = J.offs[p];
     const int L = J.lens[p];
@@ -66,26 +118,45 @@ __device__ __forceinline__ void process_program(const JobDev &J, int64_t p, int 
     const int nval = static_cast<int>(min(static_cast<int64_t>(tile), J.N - tstart));
     const int rows = J.rows;
 
+    TileValues<T, K> vals;
+    vals.buf = fbuf;
     bool anybad = pk.const_bad;
-    for (int c0 = 0; c0 < nval; c0 += CH) {
-        const float *xrow = xs + (c0 / kBox) * rows * kBox + (c0 % kBox) + lane * K;
-        T f[K];
-        bool bad[K];
-        if constexpr (sizeof(T) == 4 && K == 4)
-            run_program_ptx4(smem_addr(pbuf), smem_addr(xrow), smem_addr(stk + lane * K), f, bad);
-        else
-            run_program<T, K>(smem_addr(pbuf), pk.n, smem_addr(xrow), smem_addr(stk + lane * K),
-                              f, bad);
-        sts_vec<T, K>(smem_addr(fbuf + c0 + lane * K), f);
+    if constexpr (kRegs) {   // one pass: the whole 256-case tile
+        bool bad[8];
+        run_program_ptx8(smem_addr(pbuf), smem_addr(xs + lane * 4), smem_addr(stk + lane * 4),
+                         vals.r, bad);
 #pragma unroll
-        for (int j = 0; j < K; ++j)
-            if (bad[j] && c0 + lane * K + j < nval) anybad = true;
+        for (int j = 0; j < 8; ++j)
+            if (bad[j] && (j >> 2) * 128 + lane * 4 + (j & 3) < nval) anybad = true;
+    } else {
+        for (int c0 = 0; c0 < nval; c0 += CH) {
+            const float *xrow = xs + (c0 / kBox) * rows * kBox + (c0 % kBox) + lane * K;
+            T f[K];
+            bool bad[K];
+            if constexpr (sizeof(T) == 4 && K == 4)
+                run_program_ptx4(smem_addr(pbuf), smem_addr(xrow), smem_addr(stk + lane * K), f,
+                                 bad);
+            else
+                run_program<T, K>(smem_addr(pbuf), pk.n, smem_addr(xrow),
+                                  smem_addr(stk + lane * K), f, bad);
+            sts_vec<T, K>(smem_addr(fbuf + c0 + lane * K), f);
+#pragma unroll
+            for (int j = 0; j < K; ++j)
+                if (bad[j] && c0 + lane * K + j < nval) anybad = true;
+        }
     }
     anybad = __any_sync(kFull, anybad);
     __syncwarp();
+    const int halves = (nval + 127) / 128;
     if (J.fout) {   // per-case outputs requested (beagle_eval)
         T *dst = static_cast<T *>(J.fout) + p * J.N + tstart;
-        for (int i = lane; i < nval; i += 32) dst[i] = fbuf[i];
+        vals.for_halves(halves, lane, [&](int h, const T (&v)[4]) {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int i = h * 128 + lane * 4 + j;
+                if (i < nval) dst[i] = v[j];
+            }
+        });
     }
     if (anybad) {
         if (lane == 0) *field(kTileFlags) = TF_INVALID;
@@ -95,24 +166,39 @@ __device__ __forceinline__ void process_program(const JobDev &J, int64_t p, int 
     // Two passes over the tile's outputs: the tile mean first, then sums centred on it.
     // Valid values reach 1e30, so on the FP32 path each sum is taken over terms scaled by an
     // exact power of two 2^-k (k = 0 unless the tile holds values above 2^50); the finalize
-    // kernel multiplies back in fp64.
+    // kernel multiplies back in fp64. Lane l's targets for half h are 4 consecutive floats.
     const float *yrow = xs + J.d * kBox;          // target row
     const float *ycrow = xs + (J.d + 1) * kBox;   // centred-target row
-    auto at = [&](const float *row, int i) { return row[(i / kBox) * rows * kBox + (i % kBox)]; };
-    const T f0 = fbuf[0];
+    auto row4 = [&](const float *row, int h) {
+        const int i = h * 128 + lane * 4;
+        return *reinterpret_cast<const float4 *>(row + (i / kBox) * rows * kBox + (i % kBox));
+    };
+    auto elem = [](const float4 &v, int j) {
+        return j == 0 ? v.x : j == 1 ? v.y : j == 2 ? v.z : v.w;
+    };
+    T v0[4];
+    vals.get4(0, 0, v0);
+    const T f0 = __shfl_sync(kFull, v0[0], 0);
     Sum sf;
     bool nonconst = false;
     float emax = 0.0f, fmax_ = 0.0f, ymax = 0.0f;
-    for (int i = lane; i < nval; i += 32) {
-        const T fi = fbuf[i];
-        sf.add(fi);
-        nonconst |= (fi != f0);
-        if constexpr (sizeof(T) == 4) {
-            emax = fmaxf(emax, fabsf(fi - at(yrow, i)));
-            fmax_ = fmaxf(fmax_, fabsf(fi));
-            ymax = fmaxf(ymax, fabsf(at(ycrow, i)));
+    vals.for_halves(halves, lane, [&](int h, const T (&v)[4]) {
+        const float4 y4 = row4(yrow, h);
+        const float4 yc4 = row4(ycrow, h);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            if (h * 128 + lane * 4 + j < nval) {
+                const T fi = v[j];
+                sf.add(fi);
+                nonconst |= (fi != f0);
+                if constexpr (sizeof(T) == 4) {
+                    emax = fmaxf(emax, fabsf(fi - elem(y4, j)));
+                    fmax_ = fmaxf(fmax_, fabsf(fi));
+                    ymax = fmaxf(ymax, fabsf(elem(yc4, j)));
+                }
+            }
         }
-    }
+    });
     nonconst = __any_sync(kFull, nonconst);
     sf.warp_allreduce();
     int ke = 0, kd = 0, ky = 0;
@@ -135,20 +221,28 @@ __device__ __forceinline__ void process_program(const JobDev &J, int64_t p, int 
     if constexpr (sizeof(T) == 4) m = nonconst ? (sf.s + sf.c) / static_cast<float>(nval) : f0;
     else m = nonconst ? sf.s / static_cast<double>(nval) : f0;
     Sum se, sd, sdd, sdy;
-    for (int i = lane; i < nval; i += 32) {
-        const T fi = fbuf[i];
-        const T e = (fi - static_cast<T>(at(yrow, i))) * se_scale;
-        se.add_prod(e, e);
-        if (nonconst) {
-            const T dv = (fi - m) * sd_scale;
-            sd.add(dv);
-            sdd.add_prod(dv, dv);
-            // FP32: the stored fp32 y - ybar; FP64: y - ybar formed in fp64.
-            const T yc = sizeof(T) == 4 ? static_cast<T>(at(ycrow, i))
-                                        : static_cast<T>(at(yrow, i)) - static_cast<T>(J.ybar);
-            sdy.add_prod(dv, yc * sy_scale);
+    vals.for_halves(halves, lane, [&](int h, const T (&v)[4]) {
+        const float4 y4 = row4(yrow, h);
+        const float4 yc4 = row4(ycrow, h);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            if (h * 128 + lane * 4 + j < nval) {
+                const T fi = v[j];
+                const T e = (fi - static_cast<T>(elem(y4, j))) * se_scale;
+                se.add_prod(e, e);
+                if (nonconst) {
+                    const T dv = (fi - m) * sd_scale;
+                    sd.add(dv);
+                    sdd.add_prod(dv, dv);
+                    // FP32: the stored fp32 y - ybar; FP64: y - ybar formed in fp64.
+                    const T yc = sizeof(T) == 4 ? static_cast<T>(elem(yc4, j))
+                                                : static_cast<T>(elem(y4, j)) -
+                                                      static_cast<T>(J.ybar);
+                    sdy.add_prod(dv, yc * sy_scale);
+                }
+            }
         }
-    }
+    });
     se.warp_allreduce();
     if (nonconst) {
         sd.warp_allreduce();

@@ -179,8 +179,9 @@ beagle_status launch_batch(beagle_server *s, std::vector<std::shared_ptr<Request
     }
     beagle_status st = e == cudaSuccess ? BEAGLE_OK : cuda_fail(e, "serve: copy in");
     if (st == BEAGLE_OK) {
-        Tune fixed;
-        fixed.tile = 512;   // fixed tile: results independent of what else is in the launch
+        Tune fixed;   // fixed shape: results independent of what else is in the launch
+        fixed.cases = kCasesFp32;
+        fixed.tile = tile_for(s->cfg.precision, kCasesFp32, 0);
         st = score_jobs(jobs.data(), static_cast<int>(jobs.size()), s->cfg.precision, b.stream,
                         &fixed);
     }

@@ -66,7 +66,7 @@ extern "C" beagle_status beagle_score_static(const uint8_t *programs, const int6
         return fail(BEAGLE_ERR_ARG, "null pointer argument");
 
     // Same launch plan as beagle_score for one job.
-    const int tile = 512;
+    const int tile = tile_for(precision, kCasesFp32, 0);
     const int32_t tiles = static_cast<int32_t>((ds->N + tile - 1) / tile);
     const size_t part_bytes = static_cast<size_t>(kNumFields) * tiles * static_cast<size_t>(P) *
                               sizeof(uint32_t);
