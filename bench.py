@@ -172,6 +172,21 @@ def cpu_baseline(pr, seconds: float, threads: int = 0):
                       f"oracle, {dt:.1f} s wall"}
 
 
+def max_over_ranks(value: float, dist, device: str) -> float:
+    """The slowest rank's time (the job ends when every rank has finished); identity on 1."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_gpops(node_evals_per_rank_step: int, steps: int, world: int, ms: float) -> float:
+    """Weak scaling: every rank scores its own population of the same size each step."""
+    return node_evals_per_rank_step * steps * world / (ms / 1e3) / 1e9
+
+
 def run_reference(args, rank, world):
     """The oracle timed as the reference arm: each step scores a bounded seeded sample."""
     if rank != 0:
@@ -505,10 +520,7 @@ def main():
     kern_ms, kern_launches = beagle.kernel_time()
     step_ms = [a.elapsed_time(b) for a, b in evs]
     tot_ms = sum(step_ms)
-    if dist is not None:
-        t = torch.tensor([tot_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        tot_ms = float(t.item())
+    tot_ms = max_over_ranks(tot_ms, dist, "cuda")
     fp32 = beagle.unpack_fitness(out)
 
     # plain FP64 path (same workload, fewer steps)
@@ -559,7 +571,7 @@ def main():
     srt = sorted(step_ms)
     line = {
         "metric": METRIC,
-        "value": node_evals * args.steps * world / (tot_ms / 1e3) / 1e9,
+        "value": whole_job_gpops(node_evals, args.steps, world, tot_ms),
         "unit": "GPoPs",
         "n_gpus": world,
         "steps": args.steps,
