@@ -116,7 +116,10 @@ class Clocks:
 # DRAM traffic of the scoring kernel from an ncu capture (dram__bytes_read.sum +
 # dram__bytes_write.sum of the P = 20,000 case, scaled by 5 to a full launch: traffic is per
 # program), valid only for the kernel sources it was taken on (profiles/ has the capture).
-TRAFFIC_CAPTURE = {"sources_sha256": None, "bytes_per_launch": None}
+TRAFFIC_CAPTURE = {
+    "sources_sha256": "4ebcef52112e62a55432fbb9d7b229305ca6b1a002cfe9d362916a4286cf33fb",
+    "bytes_per_launch": 38_579_200,   # (7,676,928 read + 38,912 written) x 5
+}
 
 
 def kernel_sources_sha256():

@@ -279,6 +279,12 @@ beagle_status beagle_get_launch_config(beagle_launch_config *cfg);
  */
 beagle_status beagle_measure_op_rates(double *rates, int32_t n_rates, double seconds_hint,
                                       void *stream);
+/* beagle_measure_dispatch: cost of the interpreter's token dispatch on the current device
+ * (the prefetch, mask and indexed branch every token takes, with one-instruction handlers),
+ * with warps_per_sm (1-32) warps on every SM: the mean cycles a warp spends per dispatch and
+ * the dispatches an SM completes per cycle. Synchronous, default stream, about a millisecond. */
+beagle_status beagle_measure_dispatch(int32_t warps_per_sm, double *cycles_per_dispatch,
+                                      double *dispatches_per_sm_cycle);
 beagle_status beagle_kernel_timing(int32_t enable);
 beagle_status beagle_kernel_time(double *total_ms, int64_t *launches);
 

@@ -45,6 +45,18 @@ namespace beagle {
 #define BG_PTX_XA "bfe.u32 v, %8, 8, 4;\n\tmad.lo.u32 xa, v, 1024, %14;\n\t"
 #define BG_PTX_S "mov.b32 s, %9;\n\t"
 
+// Fused division by an input or a constant: both load the divisor into a0..a3 and share one
+// copy of the four divisions (the interpreter's speed depends on its instruction footprint).
+#define BG_PTX_PDIVX_BODY                                                                  \
+    "PDIVX_%=:\n\t" BG_PTX_XA                                                              \
+    "ld.shared.v4.f32 {a0, a1, a2, a3}, [xa];\n\tbra.uni DIVTA_%=;\n"                       \
+    "PDIVC_%=:\n\t" BG_PTX_S                                                               \
+    "mov.f32 a0, s;\n\tmov.f32 a1, s;\n\tmov.f32 a2, s;\n\tmov.f32 a3, s;\n"              \
+    "DIVTA_%=:\n\t"                                                                         \
+    BG_PTX_PDIV("%0", "%0", "a0") BG_PTX_PDIV("%1", "%1", "a1")                            \
+    BG_PTX_PDIV("%2", "%2", "a2") BG_PTX_PDIV("%3", "%3", "a3")                            \
+    BG_PTX_TRACK4 BG_PTX_DISPATCH
+
 #define BG_PTX_INTERP4                                                                     \
     "{\n\t"                                                                                \
     ".reg .pred q;\n\t"                                                                    \
@@ -110,11 +122,7 @@ namespace beagle {
     "mul.rn.f32 %0, %0, a0;\n\tmul.rn.f32 %1, %1, a1;\n\t"                                 \
     "mul.rn.f32 %2, %2, a2;\n\tmul.rn.f32 %3, %3, a3;\n\t"                                 \
     BG_PTX_TRACK4 BG_PTX_DISPATCH                                                          \
-    "PDIVX_%=:\n\t" BG_PTX_XA                                                              \
-    "ld.shared.v4.f32 {a0, a1, a2, a3}, [xa];\n\t"                                         \
-    BG_PTX_PDIV("%0", "%0", "a0") BG_PTX_PDIV("%1", "%1", "a1")                            \
-    BG_PTX_PDIV("%2", "%2", "a2") BG_PTX_PDIV("%3", "%3", "a3")                            \
-    BG_PTX_TRACK4 BG_PTX_DISPATCH                                                          \
+    BG_PTX_PDIVX_BODY                                                                      \
     "ADDC_%=:\n\t" BG_PTX_S                                                                \
     "add.rn.f32 %0, %0, s;\n\tadd.rn.f32 %1, %1, s;\n\t"                                   \
     "add.rn.f32 %2, %2, s;\n\tadd.rn.f32 %3, %3, s;\n\t"                                   \
@@ -122,10 +130,6 @@ namespace beagle {
     "MULC_%=:\n\t" BG_PTX_S                                                                \
     "mul.rn.f32 %0, %0, s;\n\tmul.rn.f32 %1, %1, s;\n\t"                                   \
     "mul.rn.f32 %2, %2, s;\n\tmul.rn.f32 %3, %3, s;\n\t"                                   \
-    BG_PTX_TRACK4 BG_PTX_DISPATCH                                                          \
-    "PDIVC_%=:\n\t" BG_PTX_S                                                               \
-    BG_PTX_PDIV("%0", "%0", "s") BG_PTX_PDIV("%1", "%1", "s")                              \
-    BG_PTX_PDIV("%2", "%2", "s") BG_PTX_PDIV("%3", "%3", "s")                              \
     BG_PTX_TRACK4 BG_PTX_DISPATCH                                                          \
     "END_%=:\n\tmov.u32 %13, 0;\n"                                                         \
     "OUT_%=:\n\t"                                                                          \
@@ -182,5 +186,6 @@ __device__ __forceinline__ void run_program_ptx4(uint32_t prog, uint32_t xrow, u
 #undef BG_PTX_XA
 #undef BG_PTX_S
 #undef BG_PTX_TBLPAD
+#undef BG_PTX_PDIVX_BODY
 
 }  // namespace beagle

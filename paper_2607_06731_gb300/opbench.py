@@ -1,6 +1,7 @@
 """Per-operator throughput of the scoring kernel on single-operator program chains.
 
     python -m paper_2607_06731_gb300.opbench [--kind ADDX,SIN,...] [--P 20000] [--reps 5]
+    python -m paper_2607_06731_gb300.opbench --dispatch
 
 Each population holds P copies of one chain (e.g. ``x0 x1 ADD x2 ADD ...`` for ADDX, the
 fused leaf-then-add handler; ``x0 SIN SIN ...`` for SIN) on N = 1024 cases, d = 5. Prints
@@ -82,15 +83,32 @@ def run(kinds, P=20000, reps=5, N=1024, d=5):
     return out_rows
 
 
+def dispatch(warps=(1, 4, 8, 16, 24, 32)):
+    """Cost of the bare token dispatch (beagle_measure_dispatch) at several warps per SM."""
+    rows = []
+    for w in warps:
+        c, r = beagle.measure_dispatch(w)
+        row = {"warps_per_sm": w, "cycles_per_dispatch": round(c, 1),
+               "dispatches_per_sm_cycle": round(r, 4)}
+        rows.append(row)
+        print(json.dumps(row), flush=True)
+    return rows
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--kind", default=",".join(KINDS))
     ap.add_argument("--P", type=int, default=20000)
     ap.add_argument("--reps", type=int, default=5)
+    ap.add_argument("--dispatch", action="store_true",
+                    help="measure the bare token dispatch instead")
     a = ap.parse_args()
     from . import build
     build.build()
-    run(a.kind.split(","), a.P, a.reps)
+    if a.dispatch:
+        dispatch()
+    else:
+        run(a.kind.split(","), a.P, a.reps)
 
 
 if __name__ == "__main__":
