@@ -357,8 +357,10 @@ def _run_c4(args, beagle, synth, torch, stream, flush, rates, clocks):
             beagle.score_programs(dp, ds, out=out, stream=stream)
     ms1 = _timed_steps(one_by_one, max(1, min(3, args.steps)), 1, stream, flush)
     t_roof = sum(roofline_peak(pr.programs, pr.N, rates) for pr in pops)
-    launches_per_plan = (len(items) + 63) // 64 * LAUNCHES_PER_CALL
-    kern_s = kern_ms / 1e3 / 2                   # scoring-kernel time per batch
+    # scoring launches per batch (the batch is cut by input width), each with its length
+    # order and finalize kernels
+    launches_per_plan = (kern_n // 2) * LAUNCHES_PER_CALL
+    kern_s = kern_ms / 1e3 / 2                   # scoring-kernel time per batch (all launches)
     big = max(pops, key=lambda p: p.node_evals)
     return {"value": ev * len(ms) / (sum(ms) / 1e3) / 1e9, "steps": len(ms),
             "warmup": max(3, args.warmup), "ms_per_step": statistics.mean(ms),

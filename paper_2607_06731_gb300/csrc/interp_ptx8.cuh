@@ -80,6 +80,11 @@ namespace beagle {
 #define BG8_SS5 "s"
 #define BG8_SS6 "s"
 #define BG8_SS7 "s"
+// a0..a7 = s (a constant operand broadcast, so the fused-constant handlers share the code of
+// the fused-input ones: the instruction footprint decides this interpreter's speed)
+#define BG8_SET_A_S                                                                        \
+    "mov.f32 a0, s;\n\tmov.f32 a1, s;\n\tmov.f32 a2, s;\n\tmov.f32 a3, s;\n\t"             \
+    "mov.f32 a4, s;\n\tmov.f32 a5, s;\n\tmov.f32 a6, s;\n\tmov.f32 a7, s;\n\t"
 #define BG8_OP_FMA_S_T_A(D, T, A) "fma.rn.f32 " D ", s, " T ", " A ";\n\t"   // D = s*T + A
 #define BG8_OP_FMA_S_A_T(D, A, T) "fma.rn.f32 " D ", s, " A ", " T ";\n\t"   // D = s*A + T
 #define BG8_OP_MUL(D, L, R) "mul.rn.f32 " D ", " L ", " R ";\n\t"
@@ -123,15 +128,15 @@ namespace beagle {
     "abs.f32 %6, %6;\n\tsqrt.rn.f32 %6, %6;\n\tabs.f32 %7, %7;\n\tsqrt.rn.f32 %7, %7;\n\t" \
     BG8_DISPATCH                                                                           \
     "SQUARE_%=:\n\t" BG8_MAP(BG8_OP_MUL, , BG8_T, BG8_T) BG8_TRACK8 BG8_DISPATCH           \
-    "ADDSUBX_%=:\n\t" BG8_XA BG8_S BG8_LD_A("xa")                                           \
-    BG8_MAP(BG8_OP_FMA_S_A_T, , BG8_A, BG8_T) BG8_TRACK8 BG8_DISPATCH                     \
-    "MULX_%=:\n\t" BG8_XA BG8_LD_A("xa")                                                   \
-    BG8_MAP(BG8_OP_MUL, , BG8_T, BG8_A) BG8_TRACK8 BG8_DISPATCH                            \
-    "PDIVX_%=:\n\t" BG8_XA BG8_LD_A("xa")                                                  \
-    BG8_MAP(BG8_OP_PDIV, , BG8_T, BG8_A) BG8_TRACK8 BG8_DISPATCH                           \
-    "ADDC_%=:\n\t" BG8_S BG8_MAP(BG8_OP_ADD, , BG8_T, BG8_SS) BG8_TRACK8 BG8_DISPATCH      \
-    "MULC_%=:\n\t" BG8_S BG8_MAP(BG8_OP_MUL, , BG8_T, BG8_SS) BG8_TRACK8 BG8_DISPATCH      \
-    "PDIVC_%=:\n\t" BG8_S BG8_MAP(BG8_OP_PDIV, , BG8_T, BG8_SS) BG8_TRACK8 BG8_DISPATCH    \
+    "ADDSUBX_%=:\n\t" BG8_XA BG8_S BG8_LD_A("xa") "bra.uni ADDTA_%=;\n"                     \
+    "ADDC_%=:\n\t" BG8_S BG8_SET_A_S "mov.f32 s, 0f3F800000;\n"                              \
+    "ADDTA_%=:\n\t" BG8_MAP(BG8_OP_FMA_S_A_T, , BG8_A, BG8_T) BG8_TRACK8 BG8_DISPATCH       \
+    "MULX_%=:\n\t" BG8_XA BG8_LD_A("xa") "bra.uni MULTA_%=;\n"                               \
+    "MULC_%=:\n\t" BG8_S BG8_SET_A_S                                                       \
+    "MULTA_%=:\n\t" BG8_MAP(BG8_OP_MUL, , BG8_T, BG8_A) BG8_TRACK8 BG8_DISPATCH            \
+    "PDIVX_%=:\n\t" BG8_XA BG8_LD_A("xa") "bra.uni DIVTA_%=;\n"                              \
+    "PDIVC_%=:\n\t" BG8_S BG8_SET_A_S                                                      \
+    "DIVTA_%=:\n\t" BG8_MAP(BG8_OP_PDIV, , BG8_T, BG8_A) BG8_TRACK8 BG8_DISPATCH           \
     "END_%=:\n\tmov.u32 %21, 0;\n"                                                         \
     "OUT_%=:\n\t"                                                                          \
     "}"
@@ -204,5 +209,6 @@ __device__ __forceinline__ void run_program_ptx8(uint32_t prog, uint32_t xrow, u
 #undef BG8_LD_TOP
 #undef BG8_LD_A
 #undef BG8_MAP
+#undef BG8_SET_A_S
 
 }  // namespace beagle
