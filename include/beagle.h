@@ -77,6 +77,11 @@ typedef int32_t beagle_status;
 #define BEAGLE_FLAG_DEGENERATE  2u  /* output identical on every case: one_minus_r2 = 1 */
 #define BEAGLE_FLAG_MALFORMED   4u  /* failed the structural check on the device: both +inf */
 #define BEAGLE_FLAG_TIMEOUT     8u  /* a bounded device wait ran out: result not computed */
+/* Every wait inside the scoring kernels is bounded (4 s by default; the environment variable
+ * BEAGLE_WAIT_LIMIT_US, read at each launch, sets another bound). A wait that runs out ends
+ * the launch early and every result of that launch carries BEAGLE_FLAG_TIMEOUT with NaN
+ * fitness; the device context stays usable. BEAGLE_TEST_STALL=1 is a test hook that makes
+ * the waits run out (the producer warp publishes no work). */
 
 /* ---- Precision of program arithmetic ---- */
 #define BEAGLE_FP32_COMPENSATED 0   /* fp32 ops; fp32 compensated sums; fp64 cross-tile merge */

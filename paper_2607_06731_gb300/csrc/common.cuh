@@ -61,9 +61,12 @@ struct LaunchParams {
     unsigned int *counter;   // work counter (zero at launch)
     unsigned int *error;     // error word (0 = fine)
     int32_t njobs;
-    int32_t tile;            // cases per tile: 512 or 1024
+    int32_t tile;            // cases per tile: 256 or 512
     int32_t group;           // programs per work item
     int32_t xbuf_floats;     // floats per X stage buffer (max rows x tile)
+    uint64_t wait_limit_ns;  // bound of every mbarrier wait (after it: error word, exit)
+    int32_t stall_producer;  // test hook: the producer publishes nothing, so waits run out
+    int32_t pad_;
 };
 
 // Error word bits

@@ -1,6 +1,7 @@
 // Launch planning: tile size, work-item size, scratch layout and the enqueue of one
 // persistent scoring launch (plus finalize) per batch of up to kMaxJobs jobs.
 #include <algorithm>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <vector>
@@ -23,6 +24,20 @@ void keep_pool_memory(int dev) {
         cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
     }
     done.push_back(dev);
+}
+
+// Device-wait settings from the environment (read at every launch):
+//   BEAGLE_WAIT_LIMIT_US  bound of every device wait in microseconds (default 4 s);
+//   BEAGLE_TEST_STALL=1   test hook: the producer warp publishes no work, so the consumers'
+//                         waits run out and every result of the launch carries FLAG_TIMEOUT.
+void apply_wait_settings(uint64_t *limit_ns, int32_t *stall) {
+    *limit_ns = 0;
+    *stall = 0;
+    if (const char *v = std::getenv("BEAGLE_WAIT_LIMIT_US")) {
+        const long long us = std::atoll(v);
+        if (us > 0) *limit_ns = static_cast<uint64_t>(us) * 1000ull;
+    }
+    if (const char *v = std::getenv("BEAGLE_TEST_STALL")) *stall = std::atoi(v) == 1 ? 1 : 0;
 }
 
 beagle_status prepare_capture() {
@@ -98,6 +113,7 @@ beagle_status enqueue(const std::vector<Planned> &jobs, size_t b, size_t e, int 
     prm.tile = tile;
     prm.group = group;
     prm.xbuf_floats = xbuf_floats;
+    apply_wait_settings(&prm.wait_limit_ns, &prm.stall_producer);
     cudaError_t le = launch_length_order(op, s);
     if (le == cudaSuccess) {
         if constexpr (MAXJ == 1) le = launch_score(prm, precision, cases, nw, grid, s);

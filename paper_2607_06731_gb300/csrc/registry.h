@@ -72,6 +72,7 @@ void clear_tuned();
 // Everything a stream capture of score_jobs must not do the first time: set the memory pool's
 // release threshold and load the kernels. Called before capturing.
 void keep_pool_memory(int dev);
+void apply_wait_settings(uint64_t *limit_ns, int32_t *stall);
 beagle_status prepare_capture();
 
 // Enqueue scoring of n jobs on stream s (one persistent launch per 64 jobs).

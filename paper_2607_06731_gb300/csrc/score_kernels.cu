@@ -299,6 +299,7 @@ score_kernel(const __grid_constant__ LaunchParams<MAXJ> prm) {
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int tile = prm.tile;
+    const uint64_t limit = prm.wait_limit_ns ? prm.wait_limit_ns : kWaitLimitNs;
     if (threadIdx.x == 0) {
         mbar_init(&full[0], 1);
         mbar_init(&full[1], 1);
@@ -309,12 +310,14 @@ score_kernel(const __grid_constant__ LaunchParams<MAXJ> prm) {
     __syncthreads();
 
     if (warp == NW) {
-        // Producer: claim items, stage their X/y tile with TMA, publish the slot.
-        if (lane == 0) {
+        // Producer: claim items, stage their X/y tile with TMA, publish the slot. (With the
+        // test hook set it publishes nothing and issues no copy: the consumers' bounded waits
+        // run out, set the error word and return.)
+        if (lane == 0 && !prm.stall_producer) {
             int k = 0;
             for (;; ++k) {
                 const int b = k & 1;
-                if (k >= 2 && !mbar_wait(&empty[b], ((k >> 1) - 1) & 1)) {
+                if (k >= 2 && !mbar_wait(&empty[b], ((k >> 1) - 1) & 1, limit)) {
                     atomicOr(prm.error, kErrTimeoutEmpty);
                     break;
                 }
@@ -344,7 +347,7 @@ score_kernel(const __grid_constant__ LaunchParams<MAXJ> prm) {
             }
             // Let the copies this thread issued land before the CTA can exit: consumers
             // wait on every published slot, so only a timed-out run needs this wait.
-            if (k >= 1) (void)mbar_wait(&full[(k - 1) & 1], ((k - 1) >> 1) & 1);
+            if (k >= 1) (void)mbar_wait(&full[(k - 1) & 1], ((k - 1) >> 1) & 1, limit);
         }
         return;
     }
@@ -355,7 +358,7 @@ score_kernel(const __grid_constant__ LaunchParams<MAXJ> prm) {
     T *stk = stk_all + static_cast<size_t>(warp) * (Lay::stack_bytes_per_warp() / sizeof(T));
     for (int k = 0;; ++k) {
         const int b = k & 1;
-        if (!mbar_wait(&full[b], (k >> 1) & 1)) {
+        if (!mbar_wait(&full[b], (k >> 1) & 1, limit)) {
             if (lane == 0) atomicOr(prm.error, kErrTimeoutFull);
             break;
         }

@@ -125,6 +125,7 @@ extern "C" beagle_status beagle_score_static(const uint8_t *programs, const int6
     prm.tile = tile;
     prm.group = group;
     prm.xbuf_floats = xbuf_floats;
+    apply_wait_settings(&prm.wait_limit_ns, &prm.stall_producer);
     e = launch_score(prm, precision, kCasesFp32, nw, grid, s);
     if (e != cudaSuccess) return cuda_fail(e, "static scoring launch");
     return BEAGLE_OK;
