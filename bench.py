@@ -47,8 +47,9 @@ def parse():
     ap.add_argument("--P", type=int, default=100_000)
     ap.add_argument("--cpu-seconds", type=float, default=10.0,
                     help="target wall time of the CPU oracle sample")
-    ap.add_argument("--workload", choices=["c2", "c3", "c4", "c5"], default="c2",
-                    help="c2: one 100k population (default, the headline line); c3: 50k "
+    ap.add_argument("--workload", choices=["c1", "c2", "c3", "c4", "c5"], default="c2",
+                    help="c2: one 100k population (default, the headline line); c1: 1024 "
+                         "programs x 1024 cases (the oracle-sized case); c3: 50k "
                          "programs x 1e6 cases, d=10 (precision); c4: 64 ragged populations "
                          "in one graph-captured batch; c5: serving loop under Poisson load")
     ap.add_argument("--requests", type=int, default=32,
@@ -169,10 +170,19 @@ def cpu_baseline(pr, seconds: float, threads: int = 0):
     oracle.score_programs(sub, pr.X, pr.y, "fp64", nthreads=threads)
     dt = time.perf_counter() - t0
     evals = int(sub.lengths.sum()) * pr.N
-    return {"value": evals / dt / 1e9, "unit": "GPoPs", "cores": oracle.threads(),
-            "kind": "oracle",
-            "sample": f"{n2} of {pr.programs.P} programs (seeded) x all {pr.N} cases, FP64 "
-                      f"oracle, {dt:.1f} s wall"}
+    out = {"value": evals / dt / 1e9, "unit": "GPoPs", "cores": oracle.threads(),
+           "kind": "oracle",
+           "sample": f"{n2} of {pr.programs.P} programs (seeded) x all {pr.N} cases, FP64 "
+                     f"oracle, {dt:.1f} s wall"}
+    if threads == 0:   # the same oracle on one core, on a sample of about a fifth of the time
+        n1 = max(2, n2 // (5 * max(1, oracle.threads())))
+        sub1 = pr.programs.subset(idx[:n1])
+        t0 = time.perf_counter()
+        oracle.score_programs(sub1, pr.X, pr.y, "fp64", nthreads=1)
+        dt1 = time.perf_counter() - t0
+        out["single_core"] = {"value": int(sub1.lengths.sum()) * pr.N / dt1 / 1e9,
+                              "unit": "GPoPs", "sample": f"{n1} programs, {dt1:.1f} s wall"}
+    return out
 
 
 def max_over_ranks(value: float, dist, device: str) -> float:
@@ -268,8 +278,8 @@ def run_other_workload(args, rank, world, local):
     clocks = Clocks(local)
     base = {"metric": METRIC, "unit": "GPoPs", "n_gpus": world, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic"}
-    if args.workload == "c3":
-        line = _run_c3(args, beagle, synth, torch, stream, flush, rates, clocks)
+    if args.workload in ("c1", "c3"):
+        line = _run_c3(args, beagle, synth, torch, stream, flush, rates, clocks, args.workload)
     elif args.workload == "c4":
         line = _run_c4(args, beagle, synth, torch, stream, flush, rates, clocks)
     else:
@@ -279,10 +289,17 @@ def run_other_workload(args, rank, world, local):
     return 0
 
 
-def _run_c3(args, beagle, synth, torch, stream, flush, rates, clocks):
-    """50,000 programs (length U{16..64}) x 1e6 cases, d = 10, y of RMS 1e3: the precision
-    workload. FP32-compensated and plain FP64 paths, error of the first against the second."""
-    pr = synth.make_c3()
+C1_DESC = ("c1-small-1024: P=1024 programs, length U{8..32}, d=2, N=1024 cases, X~U[-3,3], "
+           "y = x0 sin(x1) + x0^2/2")
+C3_DESC = ("c3-precision-1m: P=50000 programs, length U{16..64}, d=10, N=1000000 cases, "
+           "X~N(0,1), y RMS 1e3 + N(0,1)")
+
+
+def _run_c3(args, beagle, synth, torch, stream, flush, rates, clocks, which="c3"):
+    """One population on one dataset, FP32-compensated and plain FP64 paths, the error of the
+    first against the second: the precision workload (50,000 programs, length U{16..64}, on
+    1e6 cases, d = 10, y of RMS 1e3) or the small oracle-sized one (c1)."""
+    pr = synth.make_c3() if which == "c3" else synth.make_c1()
     ds = beagle.Dataset(pr.X, pr.y)
     dp = beagle.DevicePrograms(pr.programs)
     out = torch.empty((dp.P, 3), dtype=torch.float64, device="cuda")
@@ -313,10 +330,9 @@ def _run_c3(args, beagle, synth, torch, stream, flush, rates, clocks):
     return {"value": ev * len(ms) / (sum(ms) / 1e3) / 1e9, "steps": len(ms),
             "warmup": max(3, args.warmup), "ms_per_step": statistics.mean(ms),
             "p50_ms": _pctl(ms, 0.5), "p99_ms": _pctl(ms, 0.99),
-            "config": {"workload": "c3-precision-1m: P=50000 programs, length U{16..64}, "
-                                   "d=10, N=1000000 cases, X~N(0,1), y RMS 1e3 + N(0,1)",
+            "config": {"workload": C3_DESC if which == "c3" else C1_DESC,
                        "P": dp.P, "N": pr.N, "d": pr.d, "node_evals_per_step": ev,
-                       "l2": "inputs (40 MB X) plus a 256 MiB flush before every step"},
+                       "l2": "256 MiB flush before every step"},
             "fp64": {"value": ev / (statistics.median(ms64) / 1e3) / 1e9, "unit": "GPoPs",
                      "ms_per_step": statistics.median(ms64)},
             "fp32c_error_vs_fp64_path": {"programs_compared": int(ok.sum()), **err},
