@@ -118,8 +118,8 @@ class Clocks:
 # dram__bytes_write.sum of the P = 20,000 case, scaled by 5 to a full launch: traffic is per
 # program), valid only for the kernel sources it was taken on (profiles/ has the capture).
 TRAFFIC_CAPTURE = {
-    "sources_sha256": "4ebcef52112e62a55432fbb9d7b229305ca6b1a002cfe9d362916a4286cf33fb",
-    "bytes_per_launch": 38_579_200,   # (7,676,928 read + 38,912 written) x 5
+    "sources_sha256": "15f11e06340277f67d2a1adbf22eb07fc45bbd7e6a5d76feecc81cba0898b18c",
+    "bytes_per_launch": 38_530_560,   # (7,672,064 read + 34,048 written) x 5
 }
 
 
