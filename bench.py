@@ -118,19 +118,23 @@ class Clocks:
 # dram__bytes_write.sum of the P = 20,000 case, scaled by 5 to a full launch: traffic is per
 # program), valid only for the kernel sources it was taken on (profiles/ has the capture).
 TRAFFIC_CAPTURE = {
-    "sources_sha256": "15f11e06340277f67d2a1adbf22eb07fc45bbd7e6a5d76feecc81cba0898b18c",
+    "sources_sha256": "a4360c12a0277686b6552bd6f80a5c6f3190d1cb6f8a4c9d936e04a5f4fc278f",
     "bytes_per_launch": 38_530_560,   # (7,672,064 read + 34,048 written) x 5
 }
 
 
-def kernel_sources_sha256():
+# the files that define the scoring kernel's device code
+KERNEL_SOURCES = ("common.cuh", "interp_ptx.cuh", "interp_ptx8.cuh", "score.cuh",
+                  "score_kernels.cu", "transcend.cuh")
+
+
+def kernel_sources_sha256(d=None):
     import hashlib
-    d = os.path.join(ROOT, "paper_2607_06731_gb300", "csrc")
+    d = d or os.path.join(ROOT, "paper_2607_06731_gb300", "csrc")
     h = hashlib.sha256()
-    for name in sorted(os.listdir(d)):
-        if name.endswith((".cu", ".cuh", ".h")):
-            h.update(name.encode())
-            h.update(open(os.path.join(d, name), "rb").read())
+    for name in KERNEL_SOURCES:
+        h.update(name.encode())
+        h.update(open(os.path.join(d, name), "rb").read())
     return h.hexdigest()
 
 

@@ -8,6 +8,16 @@ namespace beagle {
 constexpr int kMaxThreads = 1024;          // 31 consumer warps + 1 producer warp at most
 constexpr int kCasesFp32 = 4;              // default fitness cases per lane, FP32 path (2, 4, 8)
 
+// Programs per work item for work = sum of P x tiles over the launch: about 32 items per CTA,
+// at least two programs per consumer warp (a smaller item leaves warps waiting for the next
+// staged tile) and at most 256; a launch too small for that spreads its items over every CTA.
+inline int plan_group(int64_t work, int nw, int grid) {
+    int64_t lo = 2LL * nw;
+    if (work < lo * grid) lo = work / grid > 1 ? work / grid : 1;
+    const int64_t g = work / (32LL * grid);
+    return static_cast<int>(g < lo ? lo : (g > 256 ? 256 : g));
+}
+
 // Cases per tile for a launch shape: the 8-case FP32 path runs one 256-case tile per pass;
 // the others default to 512.
 inline int tile_for(int precision, int cases, int requested) {

@@ -226,10 +226,7 @@ beagle_status score_jobs(const JobRequest *reqs, int n, int precision, cudaStrea
             lj[i].part_bytes = static_cast<size_t>(kNumFields) * J.tiles * J.P * sizeof(uint32_t);
             work += J.P * J.tiles;
         }
-        // Programs per work item: about 32 items per CTA, at least two per consumer warp (a
-        // smaller item leaves warps waiting for the next staged tile) and at most 256.
-        int group = static_cast<int>(
-            std::min<int64_t>(256, std::max<int64_t>(2 * nw, work / (32LL * grid))));
+        int group = plan_group(work, nw, grid);
         if (cfg.group) group = cfg.group;
         const bool sort = !cfg.unsorted;
         if (lj.size() == 1)

@@ -92,8 +92,7 @@ extern "C" beagle_status beagle_score_static(const uint8_t *programs, const int6
     const int nw = plan_warps(precision, kCasesFp32, xbuf_floats, tile);
     if (nw < 1 || smem_bytes(precision, kCasesFp32, xbuf_floats, tile, nw) > kSmemBudget)
         return fail(BEAGLE_ERR_LIMIT, "shared memory plan exceeds %zu bytes", kSmemBudget);
-    const int group = static_cast<int>(
-        std::min<int64_t>(256, std::max<int64_t>(2 * nw, work / (32LL * grid))));
+    const int group = plan_group(work, nw, grid);
 
     LaunchParams<1> prm;
     std::memset(&prm, 0, sizeof prm);
