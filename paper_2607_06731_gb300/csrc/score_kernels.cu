@@ -278,9 +278,14 @@ __device__ __forceinline__ int find_job(const LaunchParams<MAXJ> &prm, int64_t i
     return j;
 }
 
+// Threads per CTA the kernel is compiled for (the register budget per thread follows from it).
+// Shared memory holds the 4-case FP32 path to at most 18 consumer warps, so 20 warps (102
+// registers a thread) cost nothing and leave the compiler room to interleave the four cases'
+// transcendentals; the 2-case path fits up to 32 warps (64 registers); the 8-case and FP64
+// paths get 16 warps (128 registers).
 template <typename T, int K>
-struct KernelThreads {   // 32 warps when a thread needs at most 64 registers, else 16
-    static constexpr int value = (sizeof(T) == 4 && K <= 4) ? 1024 : 512;
+struct KernelThreads {
+    static constexpr int value = sizeof(T) != 4 ? 512 : K == 2 ? 1024 : K == 4 ? 640 : 512;
 };
 
 template <typename T, int K, int D, int MAXJ>
