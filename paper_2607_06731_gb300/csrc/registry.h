@@ -17,7 +17,7 @@ struct Dataset {
     int32_t d = 0, rows = 0;
     int64_t npad = 0;
     float *data = nullptr;                    // device [rows][npad]
-    double *tile_sy[2] = {nullptr, nullptr};    // device, per tile size (512, 1024): sums of
+    double *tile_sy[2] = {nullptr, nullptr};    // device, per tile size (512, 256): sums of
                                                 // the stored fp32 values of y - ybar
     double *tile_sy64[2] = {nullptr, nullptr};  // same, of (double)y - ybar (FP64 path)
     CUtensorMap map;                          // box: 256 cases x rows
@@ -47,7 +47,7 @@ struct JobRequest {
 // Launch-shape overrides (0 = choose automatically).
 struct Tune {
     int group = 0;   // programs per work item
-    int tile = 0;    // cases per tile (512 or 1024)
+    int tile = 0;    // cases per tile (256 or 512)
     int grid = 0;    // CTAs
     int warps = 0;   // consumer warps per CTA (upper bound)
     int cases = 0;   // fitness cases per lane, FP32 path (2, 4, 8)
