@@ -200,12 +200,12 @@ def aggregation_error(beagle, synth, progs, pr, ds, fp32, n=2000):
     f = outs.double().cpu().numpy()
     torch.cuda.synchronize()
     y = pr.y.astype(np.float64)
-    mse = ((f - y) ** 2).mean(axis=1)
-    fc = f - f.mean(axis=1, keepdims=True)
-    yc = y - y.mean()
-    with np.errstate(invalid="ignore", divide="ignore"):
+    with np.errstate(invalid="ignore", divide="ignore", over="ignore"):   # invalid programs
+        mse = ((f - y) ** 2).mean(axis=1)
+        fc = f - f.mean(axis=1, keepdims=True)
+        yc = y - y.mean()
         r = (fc * yc).sum(axis=1) / np.sqrt((fc * fc).sum(axis=1) * (yc * yc).sum())
-    omr = 1.0 - r * r
+        omr = 1.0 - r * r
     ok = (fp32[2][idx] == 0) & np.isfinite(mse) & np.isfinite(omr)
     out = {"programs_compared": int(ok.sum())}
     for name, ref, got in (("mse", mse, fp32[0][idx]), ("one_minus_r2", omr, fp32[1][idx])):
