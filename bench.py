@@ -145,6 +145,51 @@ def captured_traffic():
     return None
 
 
+# Issue roofline from unit counts and clocks. Instructions per evaluation of each operator as
+# implemented (validity check included), total and per pipe: ncu counters
+# (smsp__inst_executed[_pipe_fma|_alu|_xu].sum) of the straight-line operator microbenchmark
+# (beagle_measure_op_rates) divided by its evaluations (profiles/op_instruction_mix.md). Peak
+# rates per SM per cycle (ncu .peak_sustained): issue 4 warp instructions, FMA pipe 4, ALU 2,
+# XU 1. Valid while the sources that define the operators hash as below.
+OP_INSTR = {
+    "sources_sha256": "f4aa6df3fc13a52df89b5446c9fd4fd8075dfae2e4923e7f5af11a52125af6ec",
+    "per_sm_cycle": {"all": 4, "fma": 4, "alu": 2, "xu": 1},
+    "per_eval": {   # opcode: (all, fma, alu, xu)
+        1: (1.875, 1.0, 0.75, 0.0), 2: (1.875, 1.0, 0.75, 0.0), 3: (1.875, 1.0, 0.75, 0.0),
+        4: (12.501, 5.126, 2.25, 2.0), 5: (31.502, 15.251, 11.75, 0.0),
+        6: (32.502, 16.001, 12.0, 0.0), 7: (9.126, 6.126, 1.625, 1.0),
+        8: (27.502, 16.126, 11.0, 0.0), 9: (12.376, 5.001, 3.0, 1.0),
+        10: (1.875, 1.0, 0.5, 0.0),
+    },
+}
+OP_SOURCES = ("common.cuh", "measure.cu", "score.cuh", "transcend.cuh")
+
+
+def issue_roofline(progs_list, sm_mhz: float, sms: int = 152):
+    """Time the op work of the populations (list of (programs, N)) needs at the issue and pipe
+    rates; leaves and stack moves are free. None if the operator table is stale."""
+    import hashlib
+    d = os.path.join(ROOT, "paper_2607_06731_gb300", "csrc")
+    h = hashlib.sha256()
+    for name in OP_SOURCES:
+        h.update(name.encode())
+        h.update(open(os.path.join(d, name), "rb").read())
+    if h.hexdigest() != OP_INSTR["sources_sha256"]:
+        return None
+    pipes = ("all", "fma", "alu", "xu")
+    inst = dict.fromkeys(pipes, 0.0)
+    for progs, N in progs_list:
+        counts = np.bincount(progs.ops, minlength=64).astype(np.float64)
+        for op, per in OP_INSTR["per_eval"].items():
+            for k, v in zip(pipes, per):
+                inst[k] += counts[op] * N * v
+    f = sm_mhz * 1e6
+    t = {k: inst[k] / (OP_INSTR["per_sm_cycle"][k] * 32 * sms * f) for k in pipes}
+    bind = max(t, key=t.get)
+    return {"seconds": t[bind], "binding": "issue" if bind == "all" else bind + " pipe",
+            "per_pipe_ms": {k: v * 1e3 for k, v in t.items()}}
+
+
 def roofline_peak(progs, N, rates):
     """ALU-issue roofline: the time straight-line compiled code would need for this op mix,
     every operator at its measured throughput (validity check included), leaves free."""
@@ -360,7 +405,9 @@ def _run_c3(args, beagle, synth, torch, stream, flush, rates, clocks, which="c3"
                      "median_rel": float(np.median(rel)), "max_rel": float(rel.max())}
     ev = pr.node_evals
     kern_s = kern_ms / max(kern_n, 1) / 1e3
-    peak = ev / roofline_peak(pr.programs, pr.N, rates) / 1e9
+    peak_straight = ev / roofline_peak(pr.programs, pr.N, rates) / 1e9
+    issue = issue_roofline([(pr.programs, pr.N)], clk["sm_mhz"] or 2070.0)
+    peak = ev / issue["seconds"] / 1e9 if issue else peak_straight
     return {"value": ev * len(ms) / (sum(ms) / 1e3) / 1e9, "steps": len(ms),
             "warmup": max(3, args.warmup), "ms_per_step": statistics.mean(ms),
             "p50_ms": _pctl(ms, 0.5), "p99_ms": _pctl(ms, 0.99),
@@ -371,7 +418,10 @@ def _run_c3(args, beagle, synth, torch, stream, flush, rates, clocks, which="c3"
                      "ms_per_step": statistics.median(ms64)},
             "fp32c_error_vs_fp64_path": {"programs_compared": int(ok.sum()), **err},
             "roofline": {"bound": "alu", "achieved": ev / kern_s / 1e9, "peak": peak,
-                         "unit": "GPoPs", "frac": ev / kern_s / 1e9 / peak, "traffic": None},
+                         "unit": "GPoPs", "frac": ev / kern_s / 1e9 / peak, "traffic": None,
+                         "peak_basis": ("issue roofline, binding: " + issue["binding"])
+                                       if issue else "straight-line per-op throughput",
+                         "peak_straight_line_ops": peak_straight},
             "cpu_baseline": cpu_baseline(pr, args.cpu_seconds),
             "gpu_launches": LAUNCHES_PER_CALL * len(ms), "clocks": clk}
 
@@ -407,6 +457,9 @@ def _run_c4(args, beagle, synth, torch, stream, flush, rates, clocks):
             beagle.score_programs(dp, ds, out=out, stream=stream)
     ms1 = _timed_steps(one_by_one, max(1, min(3, args.steps)), 1, stream, flush)
     t_roof = sum(roofline_peak(pr.programs, pr.N, rates) for pr in pops)
+    issue = issue_roofline([(pr.programs, pr.N) for pr in pops], clk["sm_mhz"] or 2070.0)
+    if issue:
+        t_roof = issue["seconds"]
     # scoring launches per batch (the batch is cut by input width), each with its length
     # order and finalize kernels
     launches_per_plan = (kern_n // 2) * LAUNCHES_PER_CALL
@@ -426,7 +479,9 @@ def _run_c4(args, beagle, synth, torch, stream, flush, rates, clocks):
             "roofline": {"bound": "alu", "achieved": ev / kern_s / 1e9 if kern_s else None,
                          "peak": ev / t_roof / 1e9, "unit": "GPoPs",
                          "frac": (ev / kern_s / 1e9) / (ev / t_roof / 1e9) if kern_s else None,
-                         "traffic": None, "kernel_launches_timed": kern_n},
+                         "traffic": None, "kernel_launches_timed": kern_n,
+                         "peak_basis": ("issue roofline, binding: " + issue["binding"])
+                                       if issue else "straight-line per-op throughput"},
             "cpu_baseline": cpu_baseline(big, args.cpu_seconds),
             "gpu_launches": launches_per_plan * len(ms), "clocks": clk}
 
@@ -626,10 +681,12 @@ def main():
     d2h = progs.P * beagle.FITNESS_DTYPE.itemsize
 
     rates = beagle.measure_op_rates(1.0, stream=stream)
-    t_roof = roofline_peak(progs, pr.N, rates)
+    t_straight = roofline_peak(progs, pr.N, rates)
     kern_avg_s = kern_ms / max(kern_launches, 1) / 1e3
     achieved = node_evals / kern_avg_s / 1e9
-    peak = node_evals / t_roof / 1e9
+    issue = issue_roofline([(progs, pr.N)], clk["sm_mhz"] or 2070.0)
+    peak_straight = node_evals / t_straight / 1e9
+    peak = node_evals / issue["seconds"] / 1e9 if issue else peak_straight
 
     if rank != 0:
         return 0
@@ -668,8 +725,14 @@ def main():
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "GPoPs",
                      "frac": achieved / peak, "traffic": captured_traffic(),
                      "traffic_unit": "bytes per launch (ncu dram read + write)",
-                     "peak_basis": "per-op throughput measured by beagle_measure_op_rates "
-                                   "on this GPU (validity check included, leaves free)",
+                     "peak_basis": ("issue roofline: the op mix's instructions (ncu counts of "
+                                    "each operator as implemented, validity check included, "
+                                    "leaves free) at 4 issues / SM / cycle, 152 SMs, the "
+                                    "measured SM clock; binding: " + issue["binding"])
+                                   if issue else "straight-line per-op throughput",
+                     "per_pipe_ms": issue["per_pipe_ms"] if issue else None,
+                     "peak_straight_line_ops": peak_straight,
+                     "frac_straight_line_ops": achieved / peak_straight,
                      "kernel_ms": kern_avg_s * 1e3},
         "cpu_baseline": cpu,
         "e2e": {"value": node_evals / statistics.median(e2e_s) / 1e9, "unit": "GPoPs",
