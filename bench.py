@@ -54,6 +54,8 @@ def parse():
                          "in one graph-captured batch; c5: serving loop under Poisson load")
     ap.add_argument("--requests", type=int, default=32,
                     help="c5: requests per load level")
+    ap.add_argument("--autotune", action="store_true",
+                    help="c1/c3/c4: let beagle_autotune pick the launch shape before timing")
     return ap.parse_args()
 
 
@@ -382,6 +384,7 @@ def _run_c3(args, beagle, synth, torch, stream, flush, rates, clocks, which="c3"
     ds = beagle.Dataset(pr.X, pr.y)
     dp = beagle.DevicePrograms(pr.programs)
     out = torch.empty((dp.P, 3), dtype=torch.float64, device="cuda")
+    tuned = beagle.autotune([(dp, ds, out)])[0] if args.autotune else None
     clocks.start()
     beagle.kernel_timing(True)
     beagle.kernel_time()
@@ -413,7 +416,7 @@ def _run_c3(args, beagle, synth, torch, stream, flush, rates, clocks, which="c3"
             "p50_ms": _pctl(ms, 0.5), "p99_ms": _pctl(ms, 0.99),
             "config": {"workload": C3_DESC if which == "c3" else C1_DESC,
                        "P": dp.P, "N": pr.N, "d": pr.d, "node_evals_per_step": ev,
-                       "l2": "256 MiB flush before every step"},
+                       "l2": "256 MiB flush before every step", "autotuned": tuned},
             "fp64": {"value": ev / (statistics.median(ms64) / 1e3) / 1e9, "unit": "GPoPs",
                      "ms_per_step": statistics.median(ms64)},
             "fp32c_error_vs_fp64_path": {"programs_compared": int(ok.sum()), **err},
@@ -437,6 +440,7 @@ def _run_c4(args, beagle, synth, torch, stream, flush, rates, clocks):
         dp = beagle.DevicePrograms(pr.programs)
         items.append((dp, ds, torch.empty((dp.P, 3), dtype=torch.float64, device="cuda")))
     ev = sum(pr.node_evals for pr in pops)
+    tuned = beagle.autotune(items)[0] if args.autotune else None
     plan = beagle.BatchPlan(items)
     clocks.start()
     ms = _timed_steps(lambda: plan.launch(stream), args.steps, args.warmup, stream, flush)
@@ -472,7 +476,7 @@ def _run_c4(args, beagle, synth, torch, stream, flush, rates, clocks):
                                    "L U{4..256}, N log-U[256,1e5], d U{1..10}, one dataset "
                                    "each; one graph-captured batch per step",
                        "populations": len(pops), "programs": int(sum(p.programs.P for p in pops)),
-                       "node_evals_per_step": ev,
+                       "node_evals_per_step": ev, "autotuned": tuned,
                        "l2": "256 MiB flush before every step"},
             "one_call_per_population": {"value": ev / (statistics.median(ms1) / 1e3) / 1e9,
                                         "unit": "GPoPs", "ms_per_step": statistics.median(ms1)},
