@@ -26,7 +26,14 @@ namespace beagle {
 // Operands: %0-%3 top of stack (4 cases), %4-%7 validity trackers, %8/%9 current token words,
 // %10/%11 next token words (prefetched), %12 shared address of the token after that, %13 exit
 // code (0 = program done, else the transcendental handler id), %14 shared address of this
-// lane's first case of input row 0, %15 shared address of this lane's slot in stack row 0.
+// lane's first case of input row 0, %15 tensor-memory address of the warp's stack row 0.
+//
+// The stack rows below the top live in tensor memory (TMEM), which this kernel has no other
+// use for: row r of the warp is the 4 columns base + 4 r of its 32-lane quarter, lane l of the
+// warp holding its 4 cases in TMEM lane quarter + l. Keeping them out of shared memory lets
+// shared memory hold more warps. A row load waits for the warp's earlier row stores
+// (tcgen05.wait::st) and for itself (tcgen05.wait::ld) before its values are used, so a value
+// popped is always the one last pushed to that row.
 // Threaded dispatch: every handler ends by advancing to the prefetched token, prefetching the
 // next one and branching through the table; the program's END token leaves the loop.
 // The table has 32 entries (ids 21-31 end the program), so the 5-bit handler field needs no
@@ -41,7 +48,13 @@ namespace beagle {
     "ld.shared.v2.u32 {%10, %11}, [%12];\n\t"                                              \
     "add.u32 %12, %12, 8;\n\t"                                                             \
     "brx.idx.uni h, TBL_%=;\n"
-#define BG_PTX_ROW "bfe.u32 v, %8, 12, 8;\n\tmad.lo.u32 rp, v, 512, %15;\n\t"
+#define BG_PTX_ROW "bfe.u32 v, %8, 12, 8;\n\tmad.lo.u32 rp, v, 4, %15;\n\t"
+// push the top (4 cases) to stack row rp; load stack row rp into D0..D3
+#define BG_PTX_STROW "tcgen05.st.sync.aligned.32x32b.x4.b32 [rp], {%0, %1, %2, %3};\n\t"
+#define BG_PTX_LDROW(D0, D1, D2, D3)                                                       \
+    "tcgen05.wait::st.sync.aligned;\n\t"                                                   \
+    "tcgen05.ld.sync.aligned.32x32b.x4.b32 {" D0 ", " D1 ", " D2 ", " D3 "}, [rp];\n\t"       \
+    "tcgen05.wait::ld.sync.aligned;\n\t"
 #define BG_PTX_XA "bfe.u32 v, %8, 8, 4;\n\tmad.lo.u32 xa, v, 1024, %14;\n\t"
 #define BG_PTX_S "mov.b32 s, %9;\n\t"
 
@@ -88,37 +101,28 @@ namespace beagle {
     "MUL_%=, PDIV_%=, SIN_%=, COS_%=, EXP_%=, PLOG_%=, PSQRT_%=, SQUARE_%=, ADDSUBX_%=, "   \
     "MULX_%=, PDIVX_%=, ADDC_%=, MULC_%=, PDIVC_%=, END_%=" BG_PTX_TBLPAD ";\n\t"          \
     BG_PTX_DISPATCH                                                                        \
-    "PUSHX_%=:\n\t" BG_PTX_ROW BG_PTX_XA                                                   \
-    "st.shared.v4.f32 [rp], {%0, %1, %2, %3};\n\t"                                         \
+    "PUSHX_%=:\n\t" BG_PTX_ROW BG_PTX_XA BG_PTX_STROW                                      \
     "ld.shared.v4.f32 {%0, %1, %2, %3}, [xa];\n\t"                                         \
     BG_PTX_DISPATCH                                                                        \
-    "PUSHC_%=:\n\t" BG_PTX_ROW BG_PTX_S                                                    \
-    "st.shared.v4.f32 [rp], {%0, %1, %2, %3};\n\t"                                         \
+    "PUSHC_%=:\n\t" BG_PTX_ROW BG_PTX_S BG_PTX_STROW                                       \
     "mov.f32 %0, s;\n\tmov.f32 %1, s;\n\tmov.f32 %2, s;\n\tmov.f32 %3, s;\n\t"             \
     BG_PTX_DISPATCH                                                                        \
-    "DUP_%=:\n\t" BG_PTX_ROW                                                               \
-    "st.shared.v4.f32 [rp], {%0, %1, %2, %3};\n\t"                                         \
+    "DUP_%=:\n\t" BG_PTX_ROW BG_PTX_STROW                                                  \
     BG_PTX_DISPATCH                                                                        \
-    "SWAP_%=:\n\t" BG_PTX_ROW                                                              \
-    "ld.shared.v4.f32 {a0, a1, a2, a3}, [rp];\n\t"                                         \
-    "st.shared.v4.f32 [rp], {%0, %1, %2, %3};\n\t"                                         \
+    "SWAP_%=:\n\t" BG_PTX_ROW BG_PTX_LDROW("a0", "a1", "a2", "a3") BG_PTX_STROW            \
     "mov.f32 %0, a0;\n\tmov.f32 %1, a1;\n\tmov.f32 %2, a2;\n\tmov.f32 %3, a3;\n\t"         \
     BG_PTX_DISPATCH                                                                        \
-    "DEL_%=:\n\t" BG_PTX_ROW                                                               \
-    "ld.shared.v4.f32 {%0, %1, %2, %3}, [rp];\n\t"                                         \
+    "DEL_%=:\n\t" BG_PTX_ROW BG_PTX_LDROW("%0", "%1", "%2", "%3")                          \
     BG_PTX_DISPATCH                                                                        \
-    "ADDSUB_%=:\n\t" BG_PTX_ROW BG_PTX_S                                                   \
-    "ld.shared.v4.f32 {a0, a1, a2, a3}, [rp];\n\t"                                         \
+    "ADDSUB_%=:\n\t" BG_PTX_ROW BG_PTX_S BG_PTX_LDROW("a0", "a1", "a2", "a3")              \
     "fma.rn.f32 %0, s, %0, a0;\n\tfma.rn.f32 %1, s, %1, a1;\n\t"                           \
     "fma.rn.f32 %2, s, %2, a2;\n\tfma.rn.f32 %3, s, %3, a3;\n\t"                           \
     BG_PTX_TRACK4 BG_PTX_DISPATCH                                                          \
-    "MUL_%=:\n\t" BG_PTX_ROW                                                               \
-    "ld.shared.v4.f32 {a0, a1, a2, a3}, [rp];\n\t"                                         \
+    "MUL_%=:\n\t" BG_PTX_ROW BG_PTX_LDROW("a0", "a1", "a2", "a3")                          \
     "mul.rn.f32 %0, a0, %0;\n\tmul.rn.f32 %1, a1, %1;\n\t"                                 \
     "mul.rn.f32 %2, a2, %2;\n\tmul.rn.f32 %3, a3, %3;\n\t"                                 \
     BG_PTX_TRACK4 BG_PTX_DISPATCH                                                          \
-    "PDIV_%=:\n\t" BG_PTX_ROW                                                              \
-    "ld.shared.v4.f32 {a0, a1, a2, a3}, [rp];\n\t"                                         \
+    "PDIV_%=:\n\t" BG_PTX_ROW BG_PTX_LDROW("a0", "a1", "a2", "a3")                         \
     BG_PTX_PDIV("%0", "a0", "%0") BG_PTX_PDIV("%1", "a1", "%1")                            \
     BG_PTX_PDIV("%2", "a2", "%2") BG_PTX_PDIV("%3", "a3", "%3")                            \
     BG_PTX_TRACK4 BG_PTX_DISPATCH                                                          \
@@ -146,10 +150,11 @@ static_assert(H_PUSHX == 0 && H_PUSHC == 1 && H_DUP == 2 && H_SWAP == 3 && H_DEL
                   H_ADDSUBX == 14 && H_MULX == 15 && H_PDIVX == 16 && H_ADDC == 17 &&
                   H_MULC == 18 && H_PDIVC == 19 && H_END == 20,
               "the PTX jump table lists the handlers in this order");
-static_assert(StackGeom<float, 4>::kRowShift == 9 && kBoxShift == 10,
-              "the PTX loop hard-codes the row and input shifts");
+static_assert(kBoxShift == 10, "the PTX loop hard-codes the input row shift");
 
-__device__ __forceinline__ void run_program_ptx4(uint32_t prog, uint32_t xrow, uint32_t stk,
+// prog: shared address of the packed program; xrow: shared address of this lane's first case
+// of input row 0; tstk: tensor-memory address of the warp's stack row 0 (4 columns a row).
+__device__ __forceinline__ void run_program_ptx4(uint32_t prog, uint32_t xrow, uint32_t tstk,
                                                  float (&top)[4], bool (&bad)[4]) {
     using A = Arith<float>;
     float t0 = 0.f, t1 = 0.f, t2 = 0.f, t3 = 0.f, m0 = 0.f, m1 = 0.f, m2 = 0.f, m3 = 0.f;
@@ -161,7 +166,7 @@ __device__ __forceinline__ void run_program_ptx4(uint32_t prog, uint32_t xrow, u
         asm volatile(BG_PTX_INTERP4
                      : "+f"(t0), "+f"(t1), "+f"(t2), "+f"(t3), "+f"(m0), "+f"(m1), "+f"(m2),
                        "+f"(m3), "+r"(cx), "+r"(cy), "+r"(nx), "+r"(ny), "+r"(pa), "=r"(code)
-                     : "r"(xrow), "r"(stk)
+                     : "r"(xrow), "r"(tstk)
                      : "memory");
         if (code == 0) break;
         switch (code) {
@@ -188,6 +193,8 @@ __device__ __forceinline__ void run_program_ptx4(uint32_t prog, uint32_t xrow, u
 #undef BG_PTX_PDIV
 #undef BG_PTX_DISPATCH
 #undef BG_PTX_ROW
+#undef BG_PTX_STROW
+#undef BG_PTX_LDROW
 #undef BG_PTX_XA
 #undef BG_PTX_S
 #undef BG_PTX_TBLPAD

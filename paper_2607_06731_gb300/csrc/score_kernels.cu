@@ -22,9 +22,41 @@ struct Slot {
     int next;       // next program of the item (shared-memory counter)
 };
 
+// Tensor memory (TMEM): allocation of ncols columns (a power of two, 32..512) by one whole
+// warp, the base address written to *dst in shared memory; the same warp frees it. The fences
+// order TMEM accesses around the CTA barriers that publish the address and end its use.
+__device__ __forceinline__ void tmem_alloc(uint32_t *dst, uint32_t ncols) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                 ::"r"(smem_addr(dst)), "r"(ncols) : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr),
+                 "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void tmem_fence_before_sync() {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_fence_after_sync() {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+// The 4-case FP32 path keeps its stack rows in tensor memory (64 columns a warp, the warp's
+// 32-lane quarter of TMEM being warp % 4 and its column slot warp / 4); the other paths keep
+// them in shared memory.
+template <typename T, int K>
+constexpr bool kTmemStackPath = sizeof(T) == 4 && K == 4;
+constexpr int kTmemColsPerWarp = 64;
+static_assert(4 * (kMaxDepth - 1) <= kTmemColsPerWarp, "a warp's stack rows fit its columns");
+__host__ __device__ constexpr uint32_t tmem_columns(int nw) {   // power of two, 32..512
+    const int need = (nw + 3) / 4 * kTmemColsPerWarp;
+    return need <= 32 ? 32u : need <= 64 ? 64u : need <= 128 ? 128u : need <= 256 ? 256u : 512u;
+}
+
 template <typename T, int K>
 struct SmemLayout {
     static constexpr size_t kStackRows = kMaxDepth - 1;
+    static constexpr bool kTmemStack = kTmemStackPath<T, K>;
     static __host__ __device__ size_t xbuf_off() { return 128; }
     static __host__ __device__ size_t fbuf_off(int xbuf_floats) {
         return xbuf_off() + 2ull * xbuf_floats * sizeof(float);
@@ -37,7 +69,7 @@ struct SmemLayout {
         return pbuf_off(xbuf_floats, tile, nw) + static_cast<size_t>(nw) * (kMaxLen + 2) * sizeof(uint2);
     }
     static __host__ __device__ size_t stack_bytes_per_warp() {
-        return kStackRows * 32 * K * sizeof(T);
+        return kTmemStack ? 0 : kStackRows * 32 * K * sizeof(T);
     }
     static __host__ __device__ size_t total(int xbuf_floats, int tile, int nw) {
         return stack_off(xbuf_floats, tile, nw) + static_cast<size_t>(nw) * stack_bytes_per_warp();
@@ -96,7 +128,7 @@ struct TileValues {
 template <typename T, int K, int D>
 __device__ __forceinline__ void process_program(const JobDev &J, int64_t p, int t, int tile,
                                                 const float *xs, uint2 *pbuf, T *fbuf, T *stk,
-                                                int lane) {
+                                                uint32_t tstk, int lane) {
     using Sum = typename SumOf<T>::type;
     constexpr bool kRegs = kOutputsInRegs<T, K>;
     constexpr int CH = 32 * K;
@@ -134,8 +166,7 @@ __device__ __forceinline__ void process_program(const JobDev &J, int64_t p, int 
             T f[K];
             bool bad[K];
             if constexpr (sizeof(T) == 4 && K == 4)
-                run_program_ptx4(smem_addr(pbuf), smem_addr(xrow), smem_addr(stk + lane * K), f,
-                                 bad);
+                run_program_ptx4(smem_addr(pbuf), smem_addr(xrow), tstk, f, bad);
             else
                 run_program<T, K>(smem_addr(pbuf), pk.n, smem_addr(xrow),
                                   smem_addr(stk + lane * K), f, bad);
@@ -279,13 +310,13 @@ __device__ __forceinline__ int find_job(const LaunchParams<MAXJ> &prm, int64_t i
 }
 
 // Threads per CTA the kernel is compiled for (the register budget per thread follows from it).
-// Shared memory holds the 4-case FP32 path to at most 18 consumer warps, so 20 warps (102
-// registers a thread) cost nothing and leave the compiler room to interleave the four cases'
-// transcendentals; the 2-case path fits up to 32 warps (64 registers); the 8-case and FP64
-// paths get 16 warps (128 registers).
+// The 4-case FP32 path, its stack in tensor memory, gets 32 warps (64 registers a thread):
+// more resident warps hide more of the dispatch latency (C2 population: 17 consumer warps
+// 2,304 GPoPs, 27 at 72 registers 2,656, 31 at 64 registers 2,738); the 2-case path also
+// fits 32 warps; the 8-case and FP64 paths get 16 warps (128 registers).
 template <typename T, int K>
 struct KernelThreads {
-    static constexpr int value = sizeof(T) != 4 ? 512 : K == 2 ? 1024 : K == 4 ? 640 : 512;
+    static constexpr int value = sizeof(T) != 4 ? 512 : K == 2 ? 1024 : K == 4 ? 1024 : 512;
 };
 
 template <typename T, int K, int D, int MAXJ>
@@ -305,6 +336,12 @@ score_kernel(const __grid_constant__ LaunchParams<MAXJ> prm) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int tile = prm.tile;
     const uint64_t limit = prm.wait_limit_ns ? prm.wait_limit_ns : kWaitLimitNs;
+    constexpr bool kTmem = kTmemStackPath<T, K>;
+    uint32_t *tmem_base = reinterpret_cast<uint32_t *>(smem + 32);
+    if constexpr (kTmem) {
+        if (warp == 0) tmem_alloc(tmem_base, tmem_columns(NW));
+        tmem_fence_before_sync();
+    }
     if (threadIdx.x == 0) {
         mbar_init(&full[0], 1);
         mbar_init(&full[1], 1);
@@ -313,6 +350,13 @@ score_kernel(const __grid_constant__ LaunchParams<MAXJ> prm) {
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
+    uint32_t tstk = 0;
+    if constexpr (kTmem) {
+        tmem_fence_after_sync();
+        // lane quarter warp % 4 (TMEM lane field, bits 16-31), column slot warp / 4
+        tstk = *tmem_base + (static_cast<uint32_t>(warp & 3) << 21) +
+               static_cast<uint32_t>((warp >> 2) * kTmemColsPerWarp);
+    }
 
     if (warp == NW) {
         // Producer: claim items, stage their X/y tile with TMA, publish the slot. (With the
@@ -384,10 +428,20 @@ score_kernel(const __grid_constant__ LaunchParams<MAXJ> prm) {
             const int64_t q = p0 + idx;
             if (q >= p1) break;
             const int64_t p = J.order ? static_cast<int64_t>(J.order[q]) : q;
-            process_program<T, K, D>(J, p, s.tile, tile, xs, pbuf, fbuf, stk, lane);
+            process_program<T, K, D>(J, p, s.tile, tile, xs, pbuf, fbuf, stk, tstk, lane);
         }
         __syncwarp();
         if (lane == 0) mbar_arrive(&empty[b]);
+    }
+    if constexpr (kTmem) {
+        // Every consumer warp gets here (the loop ends on the last slot or a timed-out wait);
+        // the allocating warp frees the columns once all of them are done with TMEM.
+        tmem_fence_before_sync();
+        asm volatile("bar.sync 1, %0;" ::"r"(NW * 32) : "memory");
+        if (warp == 0) {
+            tmem_fence_after_sync();
+            tmem_dealloc(*tmem_base, tmem_columns(NW));
+        }
     }
 }
 
@@ -525,6 +579,7 @@ size_t smem_bytes(int precision, int cases, int xbuf_floats, int tile, int nw) {
 static int max_warps(int precision, int cases) {
     if (precision == BEAGLE_FP64) return KernelThreads<double, kCasesFp64>::value / 32 - 1;
     if (cases == 8) return KernelThreads<float, 8>::value / 32 - 1;
+    if (cases == 2) return KernelThreads<float, 2>::value / 32 - 1;
     return KernelThreads<float, 4>::value / 32 - 1;
 }
 

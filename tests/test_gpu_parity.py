@@ -227,6 +227,32 @@ def test_constant_outputs_are_degenerate_across_tiles():
         assert abs(m[0] - want) <= 1e-6 * want
 
 
+def test_outliers_and_large_values_in_tile_statistics():
+    """Outputs with a few huge values (at tile starts, inside the first 128 cases, or later),
+    offsets far from zero, and outputs or targets above 2^50, which take the rerun path."""
+    rng = np.random.default_rng(11)
+    N = 3000
+    X = rng.uniform(-1, 1, size=(3, N)).astype(np.float32)
+    X[1, ::512] = 1e4                          # an outlier at every 512-case tile start
+    X[1, 256::512] = -3e3                      # ... and at the other 256-case tile starts
+    X[2, rng.integers(0, N, 12)] = 5e5         # scattered outliers
+    X[2, 700:710] = -2e5
+    y = (X[0] * 3 + 1).astype(np.float32)
+    C, L0, L1, L2 = S.CONST, S.LOAD0, S.LOAD0 + 1, S.LOAD0 + 2
+    progs = S.from_token_lists([
+        [(L1, 0)],
+        [(L1, 0), (S.SQUARE, 0)],
+        [(L2, 0), (L0, 0), (S.ADD, 0)],
+        [(L2, 0), (C, 1e4), (S.ADD, 0)],                    # offset far from zero
+        [(L0, 0), (C, 2.0 ** 52), (S.MUL, 0)],              # outputs above 2^50
+        [(L1, 0), (C, 2.0 ** 40), (S.MUL, 0)],              # above 2^50 at the outliers only
+        [(L0, 0), (C, 3.0), (S.MUL, 0), (C, 1.0), (S.ADD, 0)],   # exact fit
+    ])
+    full_check(progs, X, y)
+    yb = (X[0] * 2.0 ** 52).astype(np.float32)           # targets above 2^50
+    full_check(progs, X, yb)
+
+
 def test_empty_population():
     X = np.ones((1, 4), np.float32) * np.arange(4, dtype=np.float32)
     ds = beagle.Dataset(X, X[0])
