@@ -120,8 +120,8 @@ class Clocks:
 # dram__bytes_write.sum of the P = 20,000 case, scaled by 5 to a full launch: traffic is per
 # program), valid only for the kernel sources it was taken on (profiles/ has the capture).
 TRAFFIC_CAPTURE = {
-    "sources_sha256": "746a6f8df8b24912f77193aba26ad69dec97c66fb258ed24f85169a2dcabeee6",
-    "bytes_per_launch": 38_560_000,   # (7,677,184 read + 34,816 written) x 5
+    "sources_sha256": "6e2cc6b73fb7a86670b4d80a4f966e79fd399c602f2dbbfc78dc60cd8e3574a2",
+    "bytes_per_launch": 39_147_520,   # (7,727,360 read + 102,144 written) x 5
 }
 
 

@@ -24,9 +24,9 @@ namespace beagle {
     "div.rn.f32 z, " NUM ", " DEN ";\n\tselp.f32 " DST ", z, 0f3F800000, q;\n\t"
 
 // Operands: %0-%3 top of stack (4 cases), %4-%7 validity trackers, %8/%9 current token words,
-// %10/%11 next token words (prefetched), %12 shared address of the token after that, %13 exit
-// code (0 = program done, else the transcendental handler id), %14 shared address of this
-// lane's first case of input row 0, %15 tensor-memory address of the warp's stack row 0.
+// %10 shared address of the next token, %11 exit code (0 = program done, else the
+// transcendental handler id), %12 shared address of this lane's first case of input row 0,
+// %13 tensor-memory address of the warp's stack row 0.
 //
 // The stack rows below the top live in tensor memory (TMEM), which this kernel has no other
 // use for: row r of the warp is the 4 columns base + 4 r of its 32-lane quarter, lane l of the
@@ -34,28 +34,27 @@ namespace beagle {
 // shared memory hold more warps. A row load waits for the warp's earlier row stores
 // (tcgen05.wait::st) and for itself (tcgen05.wait::ld) before its values are used, so a value
 // popped is always the one last pushed to that row.
-// Threaded dispatch: every handler ends by advancing to the prefetched token, prefetching the
-// next one and branching through the table; the program's END token leaves the loop.
+// Threaded dispatch: every handler ends by loading the next token and branching through the
+// table on that token's handler id, which the packer stores in bits 24-28 of the current token
+// (so the branch does not wait for the load, whose latency the branch itself covers); the
+// program's END token leaves the loop.
 // The table has 32 entries (ids 21-31 end the program), so the 5-bit handler field needs no
 // clamp before the indexed branch.
 #define BG_PTX_TBLPAD \
     ", END_%=, END_%=, END_%=, END_%=, END_%=, END_%=, END_%=, END_%=, END_%=, END_%=, END_%="
-// The handler index is taken from the prefetched token first, so the indexed branch does not
-// wait on the instruction just before it.
 #define BG_PTX_DISPATCH                                                                    \
-    "and.b32 h, %10, 31;\n\t"                                                              \
-    "mov.b32 %8, %10;\n\tmov.b32 %9, %11;\n\t"                                             \
-    "ld.shared.v2.u32 {%10, %11}, [%12];\n\t"                                              \
-    "add.u32 %12, %12, 8;\n\t"                                                             \
+    "shr.b32 h, %8, 24;\n\t"                                                               \
+    "ld.shared.v2.u32 {%8, %9}, [%10];\n\t"                                                \
+    "add.u32 %10, %10, 8;\n\t"                                                             \
     "brx.idx.uni h, TBL_%=;\n"
-#define BG_PTX_ROW "bfe.u32 v, %8, 12, 8;\n\tmad.lo.u32 rp, v, 4, %15;\n\t"
+#define BG_PTX_ROW "bfe.u32 v, %8, 12, 8;\n\tmad.lo.u32 rp, v, 4, %13;\n\t"
 // push the top (4 cases) to stack row rp; load stack row rp into D0..D3
 #define BG_PTX_STROW "tcgen05.st.sync.aligned.32x32b.x4.b32 [rp], {%0, %1, %2, %3};\n\t"
 #define BG_PTX_LDROW(D0, D1, D2, D3)                                                       \
     "tcgen05.wait::st.sync.aligned;\n\t"                                                   \
     "tcgen05.ld.sync.aligned.32x32b.x4.b32 {" D0 ", " D1 ", " D2 ", " D3 "}, [rp];\n\t"       \
     "tcgen05.wait::ld.sync.aligned;\n\t"
-#define BG_PTX_XA "bfe.u32 v, %8, 8, 4;\n\tmad.lo.u32 xa, v, 1024, %14;\n\t"
+#define BG_PTX_XA "bfe.u32 v, %8, 8, 4;\n\tmad.lo.u32 xa, v, 1024, %12;\n\t"
 #define BG_PTX_S "mov.b32 s, %9;\n\t"
 
 // Fused add/subtract and multiply by an input or a constant: the constant forms load their
@@ -126,10 +125,10 @@ namespace beagle {
     BG_PTX_PDIV("%0", "a0", "%0") BG_PTX_PDIV("%1", "a1", "%1")                            \
     BG_PTX_PDIV("%2", "a2", "%2") BG_PTX_PDIV("%3", "a3", "%3")                            \
     BG_PTX_TRACK4 BG_PTX_DISPATCH                                                          \
-    "SIN_%=:\n\tmov.u32 %13, 8;\n\tbra.uni OUT_%=;\n"                                      \
-    "COS_%=:\n\tmov.u32 %13, 9;\n\tbra.uni OUT_%=;\n"                                      \
-    "EXP_%=:\n\tmov.u32 %13, 10;\n\tbra.uni OUT_%=;\n"                                     \
-    "PLOG_%=:\n\tmov.u32 %13, 11;\n\tbra.uni OUT_%=;\n"                                    \
+    "SIN_%=:\n\tmov.u32 %11, 8;\n\tbra.uni OUT_%=;\n"                                      \
+    "COS_%=:\n\tmov.u32 %11, 9;\n\tbra.uni OUT_%=;\n"                                      \
+    "EXP_%=:\n\tmov.u32 %11, 10;\n\tbra.uni OUT_%=;\n"                                     \
+    "PLOG_%=:\n\tmov.u32 %11, 11;\n\tbra.uni OUT_%=;\n"                                    \
     "PSQRT_%=:\n\t"                                                                        \
     "abs.f32 %0, %0;\n\tsqrt.rn.f32 %0, %0;\n\tabs.f32 %1, %1;\n\tsqrt.rn.f32 %1, %1;\n\t" \
     "abs.f32 %2, %2;\n\tsqrt.rn.f32 %2, %2;\n\tabs.f32 %3, %3;\n\tsqrt.rn.f32 %3, %3;\n\t" \
@@ -140,7 +139,7 @@ namespace beagle {
     BG_PTX_TRACK4 BG_PTX_DISPATCH                                                          \
     BG_PTX_ADDMUL_BODY                                                                     \
     BG_PTX_PDIVX_BODY                                                                      \
-    "END_%=:\n\tmov.u32 %13, 0;\n"                                                         \
+    "END_%=:\n\tmov.u32 %11, 0;\n"                                                         \
     "OUT_%=:\n\t"                                                                          \
     "}"
 
@@ -158,14 +157,14 @@ __device__ __forceinline__ void run_program_ptx4(uint32_t prog, uint32_t xrow, u
                                                  float (&top)[4], bool (&bad)[4]) {
     using A = Arith<float>;
     float t0 = 0.f, t1 = 0.f, t2 = 0.f, t3 = 0.f, m0 = 0.f, m1 = 0.f, m2 = 0.f, m3 = 0.f;
-    const uint2 first = lds_token(prog);
-    // The loop's first step advances to the "next" token: start with token 0 there.
-    uint32_t cx = 0u, cy = 0u, nx = first.x, ny = first.y, pa = prog + 8u;
+    // The loop's first dispatch loads token 0 and branches on the handler id in bits 24-28 of
+    // the "current" token: start with token 0's id there.
+    uint32_t cx = (lds_token(prog).x & 31u) << 24, cy = 0u, pa = prog;
     for (;;) {
         uint32_t code;
         asm volatile(BG_PTX_INTERP4
                      : "+f"(t0), "+f"(t1), "+f"(t2), "+f"(t3), "+f"(m0), "+f"(m1), "+f"(m2),
-                       "+f"(m3), "+r"(cx), "+r"(cy), "+r"(nx), "+r"(ny), "+r"(pa), "=r"(code)
+                       "+f"(m3), "+r"(cx), "+r"(cy), "+r"(pa), "=r"(code)
                      : "r"(xrow), "r"(tstk)
                      : "memory");
         if (code == 0) break;

@@ -135,6 +135,17 @@ __device__ __forceinline__ void process_program(const JobDev &J, int64_t p, int 
     const int64_t off = J.offs[p];
     const int L = J.lens[p];
     const Packed pk = pack_program<T, D>(J.ops + off, J.consts + off, L, J.d, pbuf, lane);
+    if constexpr (sizeof(T) == 4 && K == 4) {
+        // Bits 24-28 of each token: the handler id of the token after it (the 4-case
+        // interpreter branches on it while it loads that token). Each round reads, then writes.
+        for (int base = 0; base < pk.n; base += 32) {
+            const int i = base + lane;
+            const uint32_t nh = i < pk.n ? (pbuf[i + 1].x & 31u) : 0u;
+            __syncwarp();
+            if (i < pk.n) pbuf[i].x |= nh << 24;
+            __syncwarp();
+        }
+    }
 
     const int64_t P = J.P;
     const int tiles = J.tiles;
