@@ -205,10 +205,11 @@ __device__ __forceinline__ void process_program(const JobDev &J, int64_t p, int 
         return;
     }
 
-    // Two passes over the tile's outputs: the tile mean first, then sums centred on it.
-    // Valid values reach 1e30, so on the FP32 path each sum is taken over terms scaled by an
-    // exact power of two 2^-k (k = 0 unless the tile holds values above 2^50); the finalize
-    // kernel multiplies back in fp64. Lane l's targets for half h are 4 consecutive floats.
+    // Tile statistics. Lane l's targets for half h are 4 consecutive floats. The general form
+    // (FP64 path; FP32 when an output or target reaches 2^50) takes two passes over the tile's
+    // outputs: the tile mean first, then sums centred on it. Valid values reach 1e30, so on the
+    // FP32 path each sum is taken over terms scaled by an exact power of two 2^-k (k = 0 unless
+    // the tile holds values above 2^50); the finalize kernel multiplies back in fp64.
     const float *yrow = xs + J.d * kBox;          // target row
     const float *ycrow = xs + (J.d + 1) * kBox;   // centred-target row
     auto row4 = [&](const float *row, int h) {
@@ -218,6 +219,77 @@ __device__ __forceinline__ void process_program(const JobDev &J, int64_t p, int 
     auto elem = [](const float4 &v, int j) {
         return j == 0 ? v.x : j == 1 ? v.y : j == 2 ? v.z : v.w;
     };
+    if constexpr (sizeof(T) == 4) {
+        // One pass, around the mean m0 of the tile's first 128 outputs: the finalize merge
+        // cancels about as little around m0 as around the tile mean. sum e^2 has positive terms
+        // only and is a plain fp32 sum (relative error below 22 u: 16 terms a lane, then 5
+        // pairwise steps); the centred sums are compensated. No term can overflow while every
+        // output and target is below 2^50 in magnitude, the usual case; otherwise the two-pass
+        // form below scales the terms.
+        float h0[4];
+        vals.get4(0, lane, h0);
+        const int n0 = min(nval, 128);
+        float s0 = 0.0f;
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            if (lane * 4 + j < n0) s0 += h0[j];
+#pragma unroll
+        for (int o = 16; o >= 1; o >>= 1) s0 += __shfl_xor_sync(kFull, s0, o);
+        const float m0 = s0 / static_cast<float>(n0);
+        const float fa = __shfl_sync(kFull, h0[0], 0);
+        float se1 = 0.0f, fmx = 0.0f;
+        bool nc = false;
+        KahanF sd1, sdd1, sdy1;
+        vals.for_halves(halves, lane, [&](int h, const T (&v)[4]) {
+            const float4 y4 = row4(yrow, h);
+            const float4 yc4 = row4(ycrow, h);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                if (h * 128 + lane * 4 + j < nval) {
+                    const float fi = v[j];
+                    const float e = fi - elem(y4, j);
+                    se1 = fmaf(e, e, se1);
+                    fmx = fmaxf(fmx, fabsf(fi));
+                    nc |= (fi != fa);
+                    const float dv = fi - m0;
+                    sd1.add(dv);
+                    sdd1.add_prod(dv, dv);
+                    sdy1.add_prod(dv, elem(yc4, j));
+                }
+            }
+        });
+#pragma unroll
+        for (int o = 16; o >= 1; o >>= 1) fmx = fmaxf(fmx, __shfl_xor_sync(kFull, fmx, o));
+        if (J.y_small && fmx < 0x1.0p50f) {
+            nc = __any_sync(kFull, nc);
+#pragma unroll
+            for (int o = 16; o >= 1; o >>= 1) se1 += __shfl_xor_sync(kFull, se1, o);
+            if (nc) {
+                sd1.warp_allreduce();
+                sdd1.warp_allreduce();
+                sdy1.warp_allreduce();
+            } else {
+                sd1 = KahanF();
+                sdd1 = KahanF();
+                sdy1 = KahanF();
+            }
+            if (lane == 0) {
+                uint32_t w[kNumFields];
+                w[kMean] = __float_as_uint(nc ? m0 : fa);
+                w[kMean64] = 0u;
+                w[kSe2] = __float_as_uint(se1);
+                w[kSe2 + 1] = 0u;
+                put_pair(w + kSd, sd1);
+                put_pair(w + kSdd, sdd1);
+                put_pair(w + kSdy, sdy1);
+                w[kTileFlags] = nc ? TF_NONCONST : 0u;
+#pragma unroll
+                for (int f = 0; f < kNumFields; ++f) *field(f) = w[f];
+            }
+            __syncwarp();
+            return;
+        }
+    }
     T v0[4];
     vals.get4(0, 0, v0);
     const T f0 = __shfl_sync(kFull, v0[0], 0);
