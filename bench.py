@@ -154,12 +154,12 @@ def captured_traffic():
 # rates per SM per cycle (ncu .peak_sustained): issue 4 warp instructions, FMA pipe 4, ALU 2,
 # XU 1. Valid while the sources that define the operators hash as below.
 OP_INSTR = {
-    "sources_sha256": "f4aa6df3fc13a52df89b5446c9fd4fd8075dfae2e4923e7f5af11a52125af6ec",
+    "sources_sha256": "6946e19fa464a63861f2ea3a9f83222a235c8d9fea5cb21aa7ba058992d597c3",
     "per_sm_cycle": {"all": 4, "fma": 4, "alu": 2, "xu": 1},
     "per_eval": {   # opcode: (all, fma, alu, xu)
         1: (1.875, 1.0, 0.75, 0.0), 2: (1.875, 1.0, 0.75, 0.0), 3: (1.875, 1.0, 0.75, 0.0),
-        4: (12.501, 5.126, 2.25, 2.0), 5: (31.502, 15.251, 11.75, 0.0),
-        6: (32.502, 16.001, 12.0, 0.0), 7: (9.126, 6.126, 1.625, 1.0),
+        4: (12.501, 5.126, 2.25, 2.0), 5: (28.502, 17.001, 7.0, 0.0),
+        6: (29.502, 17.251, 7.75, 0.0), 7: (9.126, 6.126, 1.625, 1.0),
         8: (27.502, 16.126, 11.0, 0.0), 9: (12.376, 5.001, 3.0, 1.0),
         10: (1.875, 1.0, 0.5, 0.0),
     },

@@ -10,7 +10,7 @@
 //             pi/2 held as three fp32 parts (fused multiply-adds; the first step is exact since
 //             x and k C1 share their low bits), |r| <= pi/4 (1 % more when the rounded quotient
 //             is off by one). Quadrant q = k for sin and k + 1 for cos (cos x = sin(x + pi/2));
-//             odd q takes the cosine polynomial and q & 2 flips the sign. sin r = r + r^3 P(s),
+//             odd q takes the cosine polynomial and q & 2 flips the sign bit. sin r = r + r^3 P(s),
 //             cos r = 1 + s Q(s), s = r^2. Arguments above 65536 in magnitude (and NaN) take
 //             CUDA's sinf/cosf on the lanes that hold them.
 //   plog      ln|x| for |x| > 1e-3, else 0: |x| = m 2^e with m in [sqrt(1/2), sqrt(2)),
@@ -57,15 +57,13 @@ __device__ __forceinline__ float sincos_fast(float x, int qo) {
     r = fmaf(-kf, kPio2C3, r);
     const int q = (__float_as_int(t) - kRoundMagicBits) + qo;
     const float s = r * r;
-    const bool odd = (q & 1) != 0;
-    const float c3 = odd ? kCosQ3 : kSinP3;
-    const float c2 = odd ? kCosQ2 : kSinP2;
-    const float c1 = odd ? kCosQ1 : kSinP1;
-    const float c0 = odd ? kCosQ0 : kSinP0;
-    const float p = fmaf(fmaf(fmaf(c3, s, c2), s, c1), s, c0);
-    const float base = odd ? 1.0f : r;
-    const float v = fmaf(base * s, p, base);
-    return (q & 2) ? -v : v;
+    // Both polynomials, then a select: fewer instructions than selecting their coefficients.
+    const float ps = fmaf(fmaf(fmaf(kSinP3, s, kSinP2), s, kSinP1), s, kSinP0);
+    const float pc = fmaf(fmaf(fmaf(kCosQ3, s, kCosQ2), s, kCosQ1), s, kCosQ0);
+    const float vs = fmaf(r * s, ps, r);
+    const float vc = fmaf(s, pc, 1.0f);
+    const float v = (q & 1) ? vc : vs;
+    return __int_as_float(__float_as_int(v) ^ ((q & 2) << 30));
 }
 
 // Large arguments: one out-of-line copy of CUDA's functions, so that their long reduction
