@@ -154,13 +154,13 @@ def captured_traffic():
 # rates per SM per cycle (ncu .peak_sustained): issue 4 warp instructions, FMA pipe 4, ALU 2,
 # XU 1. Valid while the sources that define the operators hash as below.
 OP_INSTR = {
-    "sources_sha256": "6946e19fa464a63861f2ea3a9f83222a235c8d9fea5cb21aa7ba058992d597c3",
+    "sources_sha256": "a152386e14db6a7290154c6bbbc3318f18837eeda6b3a541f8be2ece400781d9",
     "per_sm_cycle": {"all": 4, "fma": 4, "alu": 2, "xu": 1},
     "per_eval": {   # opcode: (all, fma, alu, xu)
         1: (1.875, 1.0, 0.75, 0.0), 2: (1.875, 1.0, 0.75, 0.0), 3: (1.875, 1.0, 0.75, 0.0),
         4: (12.501, 5.126, 2.25, 2.0), 5: (28.502, 17.001, 7.0, 0.0),
         6: (29.502, 17.251, 7.75, 0.0), 7: (9.126, 6.126, 1.625, 1.0),
-        8: (27.502, 16.126, 11.0, 0.0), 9: (12.376, 5.001, 3.0, 1.0),
+        8: (23.502, 16.126, 7.0, 0.0), 9: (12.376, 5.001, 3.0, 1.0),
         10: (1.875, 1.0, 0.5, 0.0),
     },
 }

@@ -57,26 +57,28 @@ namespace beagle {
 #define BG_PTX_XA "bfe.u32 v, %8, 8, 4;\n\tmad.lo.u32 xa, v, 1024, %12;\n\t"
 #define BG_PTX_S "mov.b32 s, %9;\n\t"
 
-// Fused add/subtract and multiply by an input or a constant: the constant forms load their
-// operand into a0..a3 (with multiplier 1 for the add, which the fused multiply-add then rounds
-// exactly like an add) and share the input forms' code.
+// Fused add/subtract and multiply by an input or a constant, each with its own copy of the
+// arithmetic (sharing one copy through a branch measured 0.5 % slower): the input add is a
+// fused multiply-add by the sign s = +-1, rounded exactly like an add or a subtraction; the
+// constant add adds the token's constant, already negated for a subtraction.
 #define BG_PTX_ADDMUL_BODY                                                                 \
     "ADDSUBX_%=:\n\t" BG_PTX_XA BG_PTX_S                                                   \
-    "ld.shared.v4.f32 {a0, a1, a2, a3}, [xa];\n\tbra.uni ADDTA_%=;\n"                       \
-    "ADDC_%=:\n\t" BG_PTX_S                                                                \
-    "mov.f32 a0, s;\n\tmov.f32 a1, s;\n\tmov.f32 a2, s;\n\tmov.f32 a3, s;\n\t"             \
-    "mov.f32 s, 0f3F800000;\n"                                                              \
-    "ADDTA_%=:\n\t"                                                                         \
+    "ld.shared.v4.f32 {a0, a1, a2, a3}, [xa];\n\t"                                         \
     "fma.rn.f32 %0, s, a0, %0;\n\tfma.rn.f32 %1, s, a1, %1;\n\t"                           \
     "fma.rn.f32 %2, s, a2, %2;\n\tfma.rn.f32 %3, s, a3, %3;\n\t"                           \
     BG_PTX_TRACK4 BG_PTX_DISPATCH                                                          \
+    "ADDC_%=:\n\t" BG_PTX_S                                                                \
+    "add.rn.f32 %0, %0, s;\n\tadd.rn.f32 %1, %1, s;\n\t"                                   \
+    "add.rn.f32 %2, %2, s;\n\tadd.rn.f32 %3, %3, s;\n\t"                                   \
+    BG_PTX_TRACK4 BG_PTX_DISPATCH                                                          \
     "MULX_%=:\n\t" BG_PTX_XA                                                               \
-    "ld.shared.v4.f32 {a0, a1, a2, a3}, [xa];\n\tbra.uni MULTA_%=;\n"                       \
-    "MULC_%=:\n\t" BG_PTX_S                                                                \
-    "mov.f32 a0, s;\n\tmov.f32 a1, s;\n\tmov.f32 a2, s;\n\tmov.f32 a3, s;\n"              \
-    "MULTA_%=:\n\t"                                                                         \
+    "ld.shared.v4.f32 {a0, a1, a2, a3}, [xa];\n\t"                                         \
     "mul.rn.f32 %0, %0, a0;\n\tmul.rn.f32 %1, %1, a1;\n\t"                                 \
     "mul.rn.f32 %2, %2, a2;\n\tmul.rn.f32 %3, %3, a3;\n\t"                                 \
+    BG_PTX_TRACK4 BG_PTX_DISPATCH                                                          \
+    "MULC_%=:\n\t" BG_PTX_S                                                                \
+    "mul.rn.f32 %0, %0, s;\n\tmul.rn.f32 %1, %1, s;\n\t"                                   \
+    "mul.rn.f32 %2, %2, s;\n\tmul.rn.f32 %3, %3, s;\n\t"                                   \
     BG_PTX_TRACK4 BG_PTX_DISPATCH
 
 // Fused division by an input or a constant: both load the divisor into a0..a3 and share one

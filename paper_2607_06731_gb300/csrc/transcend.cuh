@@ -13,7 +13,7 @@
 //             odd q takes the cosine polynomial and q & 2 flips the sign bit. sin r = r + r^3 P(s),
 //             cos r = 1 + s Q(s), s = r^2. Arguments above 65536 in magnitude (and NaN) take
 //             CUDA's sinf/cosf on the lanes that hold them.
-//   plog      ln|x| for |x| > 1e-3, else 0: |x| = m 2^e with m in [sqrt(1/2), sqrt(2)),
+//   plog      ln|x| for |x| > 1e-3, else 0: |x| = m 2^e with m in (sqrt(1/2), sqrt(2)],
 //             ln m = f + f^2 (-1/2 + f L(f)), f = m - 1 (exact), plus e ln 2 in two parts.
 //             Only valid operands matter (finite, |x| <= 1e30): the results for others are
 //             never used, because the program is already invalid.
@@ -93,13 +93,12 @@ __device__ __forceinline__ void sincos4(float &t0, float &t1, float &t2, float &
 // ---------------------------------------------------------------- protected log
 __device__ __forceinline__ float plog_dev(float x) {
     const float a = fabsf(x);
-    int bits = __float_as_int(a);
-    int e = (bits >> 23) - 127;
-    int mb = (bits & 0x007fffff) | 0x3f800000;
-    const bool hi = mb > 0x3fb504f3;            // m > sqrt(2): take m / 2
-    mb = hi ? mb - 0x00800000 : mb;
-    e = hi ? e + 1 : e;
-    const float f = __int_as_float(mb) - 1.0f;
+    // m in [b, 2b), b = 0x3f3504f4 (just above sqrt(1/2)): adding 1.0's bits minus b's to
+    // |x|'s bits carries into the exponent field exactly when |x|'s mantissa is at least 2b, so
+    // the exponent field gives e and the low 23 bits plus b give m (no compare, no select).
+    const uint32_t ix = __float_as_uint(a) + (0x3f800000u - 0x3f3504f4u);
+    const int e = static_cast<int>(ix >> 23) - 127;
+    const float f = __uint_as_float((ix & 0x007fffffu) + 0x3f3504f4u) - 1.0f;
     float l = fmaf(fmaf(fmaf(kLogL7, f, kLogL6), f, kLogL5), f, kLogL4);
     l = fmaf(fmaf(fmaf(fmaf(l, f, kLogL3), f, kLogL2), f, kLogL1), f, kLogL0);
     const float lnm = fmaf(f * f, fmaf(f, l, -0.5f), f);
