@@ -154,7 +154,7 @@ def captured_traffic():
 # rates per SM per cycle (ncu .peak_sustained): issue 4 warp instructions, FMA pipe 4, ALU 2,
 # XU 1. Valid while the sources that define the operators hash as below.
 OP_INSTR = {
-    "sources_sha256": "a152386e14db6a7290154c6bbbc3318f18837eeda6b3a541f8be2ece400781d9",
+    "sources_sha256": "221af5e12b432ee58c984995fded1ea03ca160632f78655d5cf233273aa09447",
     "per_sm_cycle": {"all": 4, "fma": 4, "alu": 2, "xu": 1},
     "per_eval": {   # opcode: (all, fma, alu, xu)
         1: (1.875, 1.0, 0.75, 0.0), 2: (1.875, 1.0, 0.75, 0.0), 3: (1.875, 1.0, 0.75, 0.0),

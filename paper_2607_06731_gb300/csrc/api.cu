@@ -163,12 +163,6 @@ beagle_status beagle_upload_dataset(const float *X, const float *y, int64_t N, i
         yc[i] = static_cast<float>(static_cast<double>(hy[i]) - ybar);
         syy32.add(static_cast<double>(yc[i]) * static_cast<double>(yc[i]));
     }
-    {
-        float ymx = 0.0f;
-        for (int64_t i = 0; i < N; ++i)
-            ymx = std::max(ymx, std::max(std::fabs(hy[i]), std::fabs(yc[i])));
-        ds->y_small = ymx < 0x1.0p50f;
-    }
     // The FP32 path correlates outputs with these stored values, so its S_yy is theirs too
     // (1 - r^2 of an exact fit then stays at rounding level instead of 2^-24).
     ds->syy32 = syy32.value();

@@ -50,8 +50,6 @@ struct JobDev {
     int64_t N;
     int64_t item0;           // first global work item of this job
     int32_t d, rows, tiles, groups;
-    int32_t y_small;         // every stored target and centred target is below 2^50 in magnitude
-    int32_t pad_;
     double ybar, syy;
 };
 

@@ -162,7 +162,6 @@ beagle_status score_jobs(const JobRequest *reqs, int n, int precision, cudaStrea
         pj.dev.d = ds->d;
         pj.dev.rows = ds->rows;
         pj.dev.ybar = ds->ybar;
-        pj.dev.y_small = ds->y_small ? 1 : 0;
         pj.dev.syy = precision == BEAGLE_FP64 ? ds->syy : ds->syy32;
         pj.map = &ds->map;
         keep.push_back(ds);

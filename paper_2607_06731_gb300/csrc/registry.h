@@ -23,7 +23,6 @@ struct Dataset {
     CUtensorMap map;                          // box: 256 cases x rows
     double ybar = 0.0, syy = 0.0;
     double syy32 = 0.0;                         // sum of squares of the stored fp32 y - ybar
-    bool y_small = false;                       // all |y|, |y - ybar| (fp32) below 2^50
     int holds = 0;                            // serving runs that keep it resident
     ~Dataset();
 };

@@ -223,9 +223,10 @@ __device__ __forceinline__ void process_program(const JobDev &J, int64_t p, int 
         // One pass, around the mean m0 of the tile's first 128 outputs: the finalize merge
         // cancels about as little around m0 as around the tile mean. sum e^2 has positive terms
         // only and is a plain fp32 sum (relative error below 22 u: 16 terms a lane, then 5
-        // pairwise steps); the centred sums are compensated. No term can overflow while every
-        // output and target is below 2^50 in magnitude, the usual case; otherwise the two-pass
-        // form below scales the terms.
+        // pairwise steps); the centred sums are compensated. An overflow anywhere in these
+        // unscaled sums leaves an infinity or a NaN in them; then the two-pass form below,
+        // which scales the terms, runs instead (outputs or targets near 2^60 and above). The
+        // outputs are all equal exactly when the sum of |f - f_0| is 0 (no flush to zero).
         float h0[4];
         vals.get4(0, lane, h0);
         const int n0 = min(nval, 128);
@@ -237,8 +238,7 @@ __device__ __forceinline__ void process_program(const JobDev &J, int64_t p, int 
         for (int o = 16; o >= 1; o >>= 1) s0 += __shfl_xor_sync(kFull, s0, o);
         const float m0 = s0 / static_cast<float>(n0);
         const float fa = __shfl_sync(kFull, h0[0], 0);
-        float se1 = 0.0f, fmx = 0.0f;
-        bool nc = false;
+        float se1 = 0.0f, ad = 0.0f;
         KahanF sd1, sdd1, sdy1;
         vals.for_halves(halves, lane, [&](int h, const T (&v)[4]) {
             const float4 y4 = row4(yrow, h);
@@ -249,8 +249,7 @@ __device__ __forceinline__ void process_program(const JobDev &J, int64_t p, int 
                     const float fi = v[j];
                     const float e = fi - elem(y4, j);
                     se1 = fmaf(e, e, se1);
-                    fmx = fmaxf(fmx, fabsf(fi));
-                    nc |= (fi != fa);
+                    ad += fabsf(fi - fa);
                     const float dv = fi - m0;
                     sd1.add(dv);
                     sdd1.add_prod(dv, dv);
@@ -258,21 +257,21 @@ __device__ __forceinline__ void process_program(const JobDev &J, int64_t p, int 
                 }
             }
         });
+        const bool nc = __any_sync(kFull, ad != 0.0f);
 #pragma unroll
-        for (int o = 16; o >= 1; o >>= 1) fmx = fmaxf(fmx, __shfl_xor_sync(kFull, fmx, o));
-        if (J.y_small && fmx < 0x1.0p50f) {
-            nc = __any_sync(kFull, nc);
-#pragma unroll
-            for (int o = 16; o >= 1; o >>= 1) se1 += __shfl_xor_sync(kFull, se1, o);
-            if (nc) {
-                sd1.warp_allreduce();
-                sdd1.warp_allreduce();
-                sdy1.warp_allreduce();
-            } else {
-                sd1 = KahanF();
-                sdd1 = KahanF();
-                sdy1 = KahanF();
-            }
+        for (int o = 16; o >= 1; o >>= 1) se1 += __shfl_xor_sync(kFull, se1, o);
+        if (nc) {
+            sd1.warp_allreduce();
+            sdd1.warp_allreduce();
+            sdy1.warp_allreduce();
+        } else {
+            sd1 = KahanF();
+            sdd1 = KahanF();
+            sdy1 = KahanF();
+        }
+        // Identical on every lane (the reductions are symmetric), so the branch is uniform.
+        const float chk = se1 + (sd1.s + sd1.c) + (sdd1.s + sdd1.c) + (sdy1.s + sdy1.c);
+        if (isfinite(chk)) {
             if (lane == 0) {
                 uint32_t w[kNumFields];
                 w[kMean] = __float_as_uint(nc ? m0 : fa);

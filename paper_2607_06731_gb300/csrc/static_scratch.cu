@@ -116,7 +116,6 @@ extern "C" beagle_status beagle_score_static(const uint8_t *programs, const int6
     J.tiles = tiles;
     J.groups = static_cast<int32_t>((P + group - 1) / group);
     J.ybar = ds->ybar;
-    J.y_small = ds->y_small ? 1 : 0;
     J.syy = precision == BEAGLE_FP64 ? ds->syy : ds->syy32;
     prm.total_items = static_cast<int64_t>(J.groups) * tiles;
     prm.counter = reinterpret_cast<unsigned int *>(base);

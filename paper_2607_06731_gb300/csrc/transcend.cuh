@@ -81,7 +81,9 @@ __device__ __forceinline__ void sincos4(float &t0, float &t1, float &t2, float &
     t1 = sincos_fast(a1, qo);
     t2 = sincos_fast(a2, qo);
     t3 = sincos_fast(a3, qo);
-    const float big = fmaxf(fmaxf(fabsf(a0), fabsf(a1)), fmaxf(fabsf(a2), fabsf(a3)));
+    // One test for the four: their magnitudes' sum (additions, not compares) is at most the
+    // limit only if each is; NaN fails it too. Each case then decides for itself.
+    const float big = (fabsf(a0) + fabsf(a1)) + (fabsf(a2) + fabsf(a3));
     if (!(big <= kSinCosFastLimit)) {
         if (!(fabsf(a0) <= kSinCosFastLimit)) t0 = sincos_slow(a0, qo);
         if (!(fabsf(a1) <= kSinCosFastLimit)) t1 = sincos_slow(a1, qo);

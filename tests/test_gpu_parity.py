@@ -229,7 +229,8 @@ def test_constant_outputs_are_degenerate_across_tiles():
 
 def test_outliers_and_large_values_in_tile_statistics():
     """Outputs with a few huge values (at tile starts, inside the first 128 cases, or later),
-    offsets far from zero, and outputs or targets above 2^50, which take the rerun path."""
+    offsets far from zero, outputs and targets near 2^52 (unscaled sums) and outputs near 2^70,
+    whose squares overflow fp32 (the scaled two-pass sums)."""
     rng = np.random.default_rng(11)
     N = 3000
     X = rng.uniform(-1, 1, size=(3, N)).astype(np.float32)
@@ -244,12 +245,13 @@ def test_outliers_and_large_values_in_tile_statistics():
         [(L1, 0), (S.SQUARE, 0)],
         [(L2, 0), (L0, 0), (S.ADD, 0)],
         [(L2, 0), (C, 1e4), (S.ADD, 0)],                    # offset far from zero
-        [(L0, 0), (C, 2.0 ** 52), (S.MUL, 0)],              # outputs above 2^50
+        [(L0, 0), (C, 2.0 ** 52), (S.MUL, 0)],              # outputs near 2^52
+        [(L0, 0), (C, 2.0 ** 70), (S.MUL, 0)],              # squares overflow fp32: scaled path
         [(L1, 0), (C, 2.0 ** 40), (S.MUL, 0)],              # above 2^50 at the outliers only
         [(L0, 0), (C, 3.0), (S.MUL, 0), (C, 1.0), (S.ADD, 0)],   # exact fit
     ])
     full_check(progs, X, y)
-    yb = (X[0] * 2.0 ** 52).astype(np.float32)           # targets above 2^50
+    yb = (X[0] * 2.0 ** 52).astype(np.float32)           # targets near 2^52
     full_check(progs, X, yb)
 
 
