@@ -120,8 +120,8 @@ class Clocks:
 # dram__bytes_write.sum of the P = 20,000 case, scaled by 5 to a full launch: traffic is per
 # program), valid only for the kernel sources it was taken on (profiles/ has the capture).
 TRAFFIC_CAPTURE = {
-    "sources_sha256": "6e2cc6b73fb7a86670b4d80a4f966e79fd399c602f2dbbfc78dc60cd8e3574a2",
-    "bytes_per_launch": 39_147_520,   # (7,727,360 read + 102,144 written) x 5
+    "sources_sha256": "7a3898267723013071c9863a015278f879ea5688a32944704016f8f22ea3d04f",
+    "bytes_per_launch": 39_217_920,   # (7,737,088 read + 106,496 written) x 5
 }
 
 
