@@ -1,12 +1,13 @@
 // Interpreter loop for the FP32 path with 4 cases per lane, written in inline PTX so that the
 // token dispatch is one indexed branch (brx.idx over a .branchtargets table) instead of a
 // compare-and-branch tree, and each handler dispatches the next token itself. Semantics are
-// those of run_program in score.cuh, handler for handler: the same fp32 operations in the same order (.rn forms, so nothing is contracted),
-// the same protected division and square root, the same validity decisions (the tracker
-// skips the protected square root, sin, cos and the protected log, whose results are finite
-// and at most 1e15 in magnitude whenever their operand is valid). sin, cos, exp and
-// the protected log leave the loop with their handler id; the caller applies them to the top
-// of stack (transcend.cuh's branch-free sin, cos and log; CUDA's expf) and re-enters.
+// those of run_program in score.cuh, handler for handler: the same fp32 operations in the
+// same order (.rn forms, so nothing is contracted), the same protected division and square
+// root, the same validity decisions (the tracker skips the protected square root, sin, cos
+// and the protected log, whose results are finite and at most 1e15 in magnitude whenever
+// their operand is valid). sin, cos, exp and the protected log leave the loop with their
+// handler id; the caller applies them to the top of stack (transcend.cuh's branch-free sin,
+// cos and log; CUDA's expf) and re-enters.
 #pragma once
 
 #include "score.cuh"
@@ -18,10 +19,16 @@ namespace beagle {
 #define BG_PTX_TRACK4                                                                      \
     BG_PTX_TRACK("%0", "%4") BG_PTX_TRACK("%1", "%5") BG_PTX_TRACK("%2", "%6")             \
     BG_PTX_TRACK("%3", "%7")
-// dst = |den| > 1e-3 ? num / den : 1   (protected division, Section 2.10 reading)
+// dst = |den| > 1e-3 ? num / den : 1   (protected division, Section 2.10 reading). The
+// quotient is rounded to nearest by Markstein's method, without branches: y = rcp.approx(den)
+// refined by one Newton step to the correctly rounded 1/den, w = num y, then w + (num - den w) y
+// with the remainder exact by FMA (the same steps as Arith<float>::pdiv).
 #define BG_PTX_PDIV(DST, NUM, DEN)                                                         \
     "abs.f32 z, " DEN ";\n\tsetp.gt.f32 q, z, 0f3A83126F;\n\t"                             \
-    "div.rn.f32 z, " NUM ", " DEN ";\n\tselp.f32 " DST ", z, 0f3F800000, q;\n\t"
+    "neg.f32 nd, " DEN ";\n\trcp.approx.ftz.f32 y, " DEN ";\n\t"                            \
+    "fma.rn.f32 e, nd, y, 0f3F800000;\n\tfma.rn.f32 y, e, y, y;\n\t"                       \
+    "mul.rn.f32 z, " NUM ", y;\n\tfma.rn.f32 e, nd, z, " NUM ";\n\t"                        \
+    "fma.rn.f32 z, e, y, z;\n\tselp.f32 " DST ", z, 0f3F800000, q;\n\t"
 
 // Operands: %0-%3 top of stack (4 cases), %4-%7 validity trackers, %8/%9 current token words,
 // %10 shared address of the next token, %11 exit code (0 = program done, else the
@@ -97,7 +104,7 @@ namespace beagle {
     "{\n\t"                                                                                \
     ".reg .pred q;\n\t"                                                                    \
     ".reg .b32 h, v, rp, xa;\n\t"                                                          \
-    ".reg .f32 a0, a1, a2, a3, s, z;\n\t"                                                  \
+    ".reg .f32 a0, a1, a2, a3, s, z, nd, y, e;\n\t"                                                  \
     "TBL_%=: .branchtargets PUSHX_%=, PUSHC_%=, DUP_%=, SWAP_%=, DEL_%=, ADDSUB_%=, "      \
     "MUL_%=, PDIV_%=, SIN_%=, COS_%=, EXP_%=, PLOG_%=, PSQRT_%=, SQUARE_%=, ADDSUBX_%=, "   \
     "MULX_%=, PDIVX_%=, ADDC_%=, MULC_%=, PDIVC_%=, END_%=" BG_PTX_TBLPAD ";\n\t"          \

@@ -25,9 +25,14 @@ namespace beagle {
     BG8_TRACK("%0", "%8") BG8_TRACK("%1", "%9") BG8_TRACK("%2", "%10")                     \
     BG8_TRACK("%3", "%11") BG8_TRACK("%4", "%12") BG8_TRACK("%5", "%13")                   \
     BG8_TRACK("%6", "%14") BG8_TRACK("%7", "%15")
+// Protected division, the quotient rounded to nearest by Markstein's method (the steps of
+// Arith<float>::pdiv).
 #define BG8_PDIV(DST, NUM, DEN)                                                            \
     "abs.f32 z, " DEN ";\n\tsetp.gt.f32 q, z, 0f3A83126F;\n\t"                             \
-    "div.rn.f32 z, " NUM ", " DEN ";\n\tselp.f32 " DST ", z, 0f3F800000, q;\n\t"
+    "neg.f32 nd, " DEN ";\n\trcp.approx.ftz.f32 y, " DEN ";\n\t"                            \
+    "fma.rn.f32 e, nd, y, 0f3F800000;\n\tfma.rn.f32 y, e, y, y;\n\t"                       \
+    "mul.rn.f32 z, " NUM ", y;\n\tfma.rn.f32 e, nd, z, " NUM ";\n\t"                        \
+    "fma.rn.f32 z, e, y, z;\n\tselp.f32 " DST ", z, 0f3F800000, q;\n\t"
 #define BG8_TBLPAD                                                                         \
     ", END_%=, END_%=, END_%=, END_%=, END_%=, END_%=, END_%=, END_%=, END_%=, END_%=, END_%="
 // %0-%7 top of stack (8 cases), %8-%15 validity trackers, %16/%17 current token words, %18/%19
@@ -95,7 +100,7 @@ namespace beagle {
     "{\n\t"                                                                                \
     ".reg .pred q;\n\t"                                                                    \
     ".reg .b32 h, v, rp, xa;\n\t"                                                          \
-    ".reg .f32 a0, a1, a2, a3, a4, a5, a6, a7, s, z;\n\t"                                  \
+    ".reg .f32 a0, a1, a2, a3, a4, a5, a6, a7, s, z, nd, y, e;\n\t"                                  \
     "TBL_%=: .branchtargets PUSHX_%=, PUSHC_%=, DUP_%=, SWAP_%=, DEL_%=, ADDSUB_%=, "      \
     "MUL_%=, PDIV_%=, SIN_%=, COS_%=, EXP_%=, PLOG_%=, PSQRT_%=, SQUARE_%=, ADDSUBX_%=, "   \
     "MULX_%=, PDIVX_%=, ADDC_%=, MULC_%=, PDIVC_%=, END_%=" BG8_TBLPAD ";\n\t"             \

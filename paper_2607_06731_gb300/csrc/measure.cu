@@ -28,7 +28,7 @@ __global__ void __launch_bounds__(256) op_rate_kernel(float *sink, int iters, fl
             if constexpr (OPC == BEAGLE_OP_ADD) a = a + c * 1e-3f;
             else if constexpr (OPC == BEAGLE_OP_SUB) a = a - c * 1e-3f;
             else if constexpr (OPC == BEAGLE_OP_MUL) a = a * c;
-            else if constexpr (OPC == BEAGLE_OP_PDIV) a = A::pdiv(a, c);
+            else if constexpr (OPC == BEAGLE_OP_PDIV) a = A::pdiv(c, a);   // divisor varies
             else if constexpr (OPC == BEAGLE_OP_SIN) a = A::sin_(a);
             else if constexpr (OPC == BEAGLE_OP_COS) a = A::cos_(a);
             else if constexpr (OPC == BEAGLE_OP_EXP) a = A::exp_(-a);

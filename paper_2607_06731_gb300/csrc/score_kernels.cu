@@ -206,7 +206,7 @@ __device__ __forceinline__ void process_program(const JobDev &J, int64_t p, int 
     }
 
     // Tile statistics. Lane l's targets for half h are 4 consecutive floats. The general form
-    // (FP64 path; FP32 when an output or target reaches 2^50) takes two passes over the tile's
+    // (FP64 path; FP32 when the one-pass sums overflow) takes two passes over the tile's
     // outputs: the tile mean first, then sums centred on it. Valid values reach 1e30, so on the
     // FP32 path each sum is taken over terms scaled by an exact power of two 2^-k (k = 0 unless
     // the tile holds values above 2^50); the finalize kernel multiplies back in fp64.
