@@ -120,8 +120,8 @@ class Clocks:
 # dram__bytes_write.sum of the P = 20,000 case, scaled by 5 to a full launch: traffic is per
 # program), valid only for the kernel sources it was taken on (profiles/ has the capture).
 TRAFFIC_CAPTURE = {
-    "sources_sha256": "7a3898267723013071c9863a015278f879ea5688a32944704016f8f22ea3d04f",
-    "bytes_per_launch": 39_217_920,   # (7,737,088 read + 106,496 written) x 5
+    "sources_sha256": "05d93e118d78f5a86e134c1b8456dbb2f75a987b70f6aa6532d9ef352ea49dbf",
+    "bytes_per_launch": 39_307_520,   # (7,747,584 read + 113,920 written) x 5
 }
 
 
@@ -154,11 +154,11 @@ def captured_traffic():
 # rates per SM per cycle (ncu .peak_sustained): issue 4 warp instructions, FMA pipe 4, ALU 2,
 # XU 1. Valid while the sources that define the operators hash as below.
 OP_INSTR = {
-    "sources_sha256": "221af5e12b432ee58c984995fded1ea03ca160632f78655d5cf233273aa09447",
+    "sources_sha256": "b30fe1b286ede54f6cbeeaf6fc764a64abdbc3e10af3fd25838339f88896613a",
     "per_sm_cycle": {"all": 4, "fma": 4, "alu": 2, "xu": 1},
     "per_eval": {   # opcode: (all, fma, alu, xu)
         1: (1.875, 1.0, 0.75, 0.0), 2: (1.875, 1.0, 0.75, 0.0), 3: (1.875, 1.0, 0.75, 0.0),
-        4: (12.501, 5.126, 2.25, 2.0), 5: (28.502, 17.001, 7.0, 0.0),
+        4: (8.876, 5.001, 2.75, 1.0), 5: (28.502, 17.001, 7.0, 0.0),
         6: (29.502, 17.251, 7.75, 0.0), 7: (9.126, 6.126, 1.625, 1.0),
         8: (23.502, 16.126, 7.0, 0.0), 9: (12.376, 5.001, 3.0, 1.0),
         10: (1.875, 1.0, 0.5, 0.0),
