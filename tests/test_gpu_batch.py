@@ -130,6 +130,27 @@ def test_launch_configurations_agree():
     ds.release()
 
 
+def test_stack_in_tensor_memory_at_every_warp_count():
+    """The 4-case kernel allocates 64 tensor-memory columns per four consumer warps (64 at one
+    warp, 512 at 31) and gives warp w the columns of slot w / 4 in lane quarter w % 4: the same
+    bits at every warp count and with small grids, where several CTAs share an SM."""
+    pr = S.make_c2(P=1500)
+    ds = beagle.Dataset(pr.X, pr.y)
+    dp = beagle.DevicePrograms(pr.programs)
+    try:
+        beagle.set_launch_config(cases_per_lane=4, tile=512)
+        ref = beagle.unpack_fitness(beagle.score_programs(dp, ds))
+        for warps, grid in ((1, 0), (3, 0), (4, 0), (5, 0), (8, 0), (13, 0), (31, 0), (2, 7),
+                            (6, 300)):
+            beagle.set_launch_config(cases_per_lane=4, tile=512, warps=warps, grid=grid)
+            got = beagle.unpack_fitness(beagle.score_programs(dp, ds))
+            for a, b in zip(got, ref):
+                assert np.array_equal(a, b, equal_nan=True), (warps, grid)
+    finally:
+        beagle.reset_launch_config()
+    ds.release()
+
+
 def test_plan_capture_as_the_first_call_of_a_process():
     """A graph-captured plan built before any other scoring call in a fresh process (pool
     set-up and kernel loading happen before the capture begins)."""
