@@ -120,7 +120,7 @@ class Clocks:
 # dram__bytes_write.sum of the P = 20,000 case, scaled by 5 to a full launch: traffic is per
 # program), valid only for the kernel sources it was taken on (profiles/ has the capture).
 TRAFFIC_CAPTURE = {
-    "sources_sha256": "05d93e118d78f5a86e134c1b8456dbb2f75a987b70f6aa6532d9ef352ea49dbf",
+    "sources_sha256": "538eac4a4b5dbd2428a72dee4eef4f0f14249baab51ae1a2f9cb8876c8e594f1",
     "bytes_per_launch": 39_307_520,   # (7,747,584 read + 113,920 written) x 5
 }
 
@@ -154,7 +154,7 @@ def captured_traffic():
 # rates per SM per cycle (ncu .peak_sustained): issue 4 warp instructions, FMA pipe 4, ALU 2,
 # XU 1. Valid while the sources that define the operators hash as below.
 OP_INSTR = {
-    "sources_sha256": "b30fe1b286ede54f6cbeeaf6fc764a64abdbc3e10af3fd25838339f88896613a",
+    "sources_sha256": "f6dc884c9294e922d0cc50a7e86c3506fe88d9afdfd81be49e948521fe9b7ac1",
     "per_sm_cycle": {"all": 4, "fma": 4, "alu": 2, "xu": 1},
     "per_eval": {   # opcode: (all, fma, alu, xu)
         1: (1.875, 1.0, 0.75, 0.0), 2: (1.875, 1.0, 0.75, 0.0), 3: (1.875, 1.0, 0.75, 0.0),

@@ -1,10 +1,13 @@
 """The FP32 protected division against IEEE float32 division, through the interpreter.
 
 The FP32 paths divide by Markstein's method (a refined reciprocal approximation and one
-remainder correction), which must give the correctly rounded quotient wherever it is a normal
-number: every divisor mantissa is checked exhaustively, then random pairs over a wide exponent
-range, on each cases-per-lane variant. Zero quotients may differ from IEEE in the sign of zero
-only, which numeric comparison ignores.
+remainder correction). Its remainder num - den q is exact while it is a normal number, so the
+quotient is the correctly rounded one for |num| >= 2^-100 with a normal quotient: every divisor
+mantissa is checked exhaustively, then random pairs over a wide exponent range, on each
+cases-per-lane variant. Below that (numerators under 2^-100, or subnormal quotients) the
+remainder is rounded and the quotient may be one unit in the last place off: that range is
+pinned to 1 ulp. Zero quotients may differ from IEEE in the sign of zero only, which numeric
+comparison ignores.
 """
 from __future__ import annotations
 
@@ -75,3 +78,27 @@ def test_random_pairs(cases):
         return (m * np.exp2(rng.integers(-60, 61, n))).astype(np.float32)
 
     _check(draw(), draw(), cases)
+
+
+def _ulps(a: np.ndarray, b: np.ndarray) -> np.ndarray:
+    """Distance in units in the last place between same-sign finite floats (0 if equal)."""
+    ia = a.view(np.int32).astype(np.int64)
+    ib = b.view(np.int32).astype(np.int64)
+    return np.where(a == b, 0, np.abs(ia - ib))
+
+
+@pytest.mark.parametrize("cases", [4, 8])
+def test_tiny_numerators_within_one_ulp(cases):
+    """Numerators 2^-126..2^-100 over divisors 2^-9..2^20: normal quotients whose remainder can
+    be subnormal; and quotients down in the subnormal range. At most 1 ulp from IEEE."""
+    rng = np.random.default_rng(17 + cases)
+    n = 1 << 21
+    num = (rng.uniform(1, 2, n) * np.exp2(rng.integers(-126, -99, n))).astype(np.float32)
+    den = (rng.uniform(1, 2, n) * rng.choice([-1.0, 1.0], n) *
+           np.exp2(rng.integers(-9, 21, n))).astype(np.float32)
+    got = _quotients(num, den, cases)
+    want = _ieee(num, den)
+    assert np.all(np.sign(got) == np.sign(want))
+    d = _ulps(np.abs(got), np.abs(want))
+    assert d.max() <= 1, int(d.max())
+    print(f"cases {cases}: {np.mean(d > 0):.2e} of tiny-numerator quotients 1 ulp off")
