@@ -1,14 +1,19 @@
 #!/usr/bin/env python3
 """Population fitness scoring benchmark: GPoPs (program-node evaluations per second).
 
-One step = one beagle_score call over the whole population of the workload: every program
-interpreted on every fitness case and reduced to its MSE and 1 - r^2 (Beagle tutorial,
-Section 2.4). Default workload: P = 100,000 random postfix programs (length U{16..128},
-d = 5 inputs), N = 1,024 fitness cases, X ~ U[-3, 3], y = a random 20-node expression plus
-N(0, 0.01) noise, on the FP32-compensated path. Inputs are resident in HBM before timing;
-L2 is flushed (a 256 MiB write) before every timed step, outside the timed events.
+One step = one beagle_score call over a whole population: every program interpreted on
+every fitness case and reduced to its MSE and 1 - r^2 (Beagle tutorial, "Dividing Tasks
+Between CPU and GPU": one aggregated fitness per individual). The default run is the
+precision workload: P = 50,000 random postfix programs (length U{16..64}, d = 10 inputs) on
+N = 1,000,000 fitness cases, X ~ N(0, 1), y = a random 30-node expression scaled to RMS 1e3
+plus N(0, 1) noise, on the FP32-compensated path, with the plain FP64 path beside it and the
+oracle's verdict on a seeded 10,000-program sample at the full case count. The same line
+carries compact sub-lines for the small oracle-sized case, the 100,000-program population and
+the 64 ragged populations in one graph-captured batch. Inputs are resident in HBM before
+timing; L2 is flushed (a 256 MiB write) before every timed step, outside the timed events.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload headline|c1|c2|c3|c4|c5]
 
 Under torchrun each rank scores its own population (seed + rank) on its own GPU with no
 collective on the data path (weak scaling); rank 0 prints one JSON line.
@@ -17,7 +22,9 @@ from __future__ import annotations
 
 import argparse
 import json
+import multiprocessing as mp
 import os
+import shutil
 import statistics
 import subprocess
 import sys
@@ -32,30 +39,39 @@ sys.path.insert(0, ROOT)
 METRIC = "GPoPs (node-evals/s) FP32-compensated vs plain FP64 at ≤1e-5 rel err; p50/p99"
 # kernels one scoring call launches: length order, persistent scoring kernel, fp64 finalize
 LAUNCHES_PER_CALL = 3
-WORKLOAD = ("c2-population-100k: P=100000 programs, length U{16..128}, d=5, N=1024 cases, "
-            "X~U[-3,3], y=20-node expression + N(0,0.01) noise; MSE and 1-R^2")
+C1_DESC = ("c1-small-1024: P=1024 programs, length U{8..32}, d=2, N=1024 cases, X~U[-3,3], "
+           "y = x0 sin(x1) + x0^2/2; MSE")
+C2_DESC = ("c2-population-100k: P=100000 programs, length U{16..128}, d=5, N=1024 cases, "
+           "X~U[-3,3], y=20-node expression + N(0,0.01) noise; MSE and 1-R^2")
+C3_DESC = ("c3-precision-1m: P=50000 programs, length U{16..64}, d=10, N=1000000 cases, "
+           "X~N(0,1), y=30-node expression at RMS 1e3 + N(0,1) noise; FP32-compensated vs "
+           "plain FP64, error against the FP64 oracle on a 10k-program sample")
+C4_DESC = ("c4-ragged-64: 64 populations, P log-U[1e3,2e5], L U{4..256}, N log-U[256,1e5], "
+           "d U{1..10}, one dataset each; one graph-captured batch per step")
 
 
 def parse():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--fp64-steps", type=int, default=3)
-    ap.add_argument("--e2e-steps", type=int, default=5)
-    ap.add_argument("--P", type=int, default=100_000)
+    ap.add_argument("--workload", choices=["headline", "c1", "c2", "c3", "c4", "c5"],
+                    default="headline",
+                    help="headline (default): the precision workload with oracle gates and "
+                         "compact c1/c2/c4 sub-lines; c1..c5: one workload on its own line")
+    ap.add_argument("--fp64-steps", type=int, default=1)
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--parity-sample", type=int, default=10_000,
+                    help="programs of the timed launch checked against the oracle at the full "
+                         "case count (0: skip)")
     ap.add_argument("--cpu-seconds", type=float, default=10.0,
                     help="target wall time of the CPU oracle sample")
-    ap.add_argument("--workload", choices=["c1", "c2", "c3", "c4", "c5"], default="c2",
-                    help="c2: one 100k population (default, the headline line); c1: 1024 "
-                         "programs x 1024 cases (the oracle-sized case); c3: 50k "
-                         "programs x 1e6 cases, d=10 (precision); c4: 64 ragged populations "
-                         "in one graph-captured batch; c5: serving loop under Poisson load")
-    ap.add_argument("--requests", type=int, default=32,
-                    help="c5: requests per load level")
+    ap.add_argument("--P", type=int, default=0, help="override the population size")
+    ap.add_argument("--requests", type=int, default=200, help="c5: requests per load level")
     ap.add_argument("--autotune", action="store_true",
-                    help="c1/c3/c4: let beagle_autotune pick the launch shape before timing")
+                    help="let beagle_autotune pick the launch shape before timing")
+    ap.add_argument("--no-sub", action="store_true", help="headline without the sub-lines")
     return ap.parse_args()
 
 
@@ -116,90 +132,201 @@ class Clocks:
                 "samples": len(sm)}
 
 
-# DRAM traffic of the scoring kernel from an ncu capture (dram__bytes_read.sum +
-# dram__bytes_write.sum of the P = 20,000 case, scaled by 5 to a full launch: traffic is per
-# program), valid only for the kernel sources it was taken on (profiles/ has the capture).
-TRAFFIC_CAPTURE = {
-    "sources_sha256": "538eac4a4b5dbd2428a72dee4eef4f0f14249baab51ae1a2f9cb8876c8e594f1",
-    "bytes_per_launch": 39_307_520,   # (7,747,584 read + 113,920 written) x 5
-}
+# ----------------------------------------------------------------------------- roofline
+# Algorithmic operations per node evaluation (the method's own arithmetic; leaves and stack
+# moves cost nothing), by opcode: (FP32 pipe, MUFU/XU pipe, ALU pipe) lane operations. Every
+# operator also pays one validity compare on the ALU pipe.
+#   add/sub/mul/square  1 FP32                    + 1 ALU
+#   protected divide    3 FP32 + 1 MUFU (rcp)     + 2 ALU (threshold select, validity)
+#   sin, cos            4 FP32 + 1 MUFU           + 1 ALU
+#   exp                 2 FP32 + 1 MUFU (ex2)     + 1 ALU
+#   protected log       1 FP32 + 1 MUFU (lg2)     + 2 ALU (threshold select, validity)
+#   protected sqrt      2 FP32 + 1 MUFU (rsq)     + 1 ALU
+ALGO_UNITS = {1: (1, 0, 1), 2: (1, 0, 1), 3: (1, 0, 1), 10: (1, 0, 1),
+              4: (3, 1, 2), 5: (4, 1, 1), 6: (4, 1, 1), 7: (2, 1, 1), 8: (1, 1, 2),
+              9: (2, 1, 1)}
+# Lanes per SM per clock of each pipe on GB300 (ncu .peak_sustained: FMA 4, ALU 2, XU 1 warp
+# instructions per SM per cycle) and the issue limit (4 warp instructions per SM per cycle).
+LANES_PER_SM_CLK = {"fp32": 128, "mufu": 32, "alu": 64, "issue": 128}
 
 
-# the files that define the scoring kernel's device code
-KERNEL_SOURCES = ("common.cuh", "interp_ptx.cuh", "interp_ptx8.cuh", "score.cuh",
-                  "score_kernels.cu", "transcend.cuh")
-
-
-def kernel_sources_sha256(d=None):
-    import hashlib
-    d = d or os.path.join(ROOT, "paper_2607_06731_gb300", "csrc")
-    h = hashlib.sha256()
-    for name in KERNEL_SOURCES:
-        h.update(name.encode())
-        h.update(open(os.path.join(d, name), "rb").read())
-    return h.hexdigest()
-
-
-def captured_traffic():
-    cap = TRAFFIC_CAPTURE
-    if cap["sources_sha256"] and cap["sources_sha256"] == kernel_sources_sha256():
-        return cap["bytes_per_launch"]
-    return None
-
-
-# Issue roofline from unit counts and clocks. Instructions per evaluation of each operator as
-# implemented (validity check included), total and per pipe: ncu counters
-# (smsp__inst_executed[_pipe_fma|_alu|_xu].sum) of the straight-line operator microbenchmark
-# (beagle_measure_op_rates) divided by its evaluations (profiles/op_instruction_mix.md). Peak
-# rates per SM per cycle (ncu .peak_sustained): issue 4 warp instructions, FMA pipe 4, ALU 2,
-# XU 1. Valid while the sources that define the operators hash as below.
-OP_INSTR = {
-    "sources_sha256": "f6dc884c9294e922d0cc50a7e86c3506fe88d9afdfd81be49e948521fe9b7ac1",
-    "per_sm_cycle": {"all": 4, "fma": 4, "alu": 2, "xu": 1},
-    "per_eval": {   # opcode: (all, fma, alu, xu)
-        1: (1.875, 1.0, 0.75, 0.0), 2: (1.875, 1.0, 0.75, 0.0), 3: (1.875, 1.0, 0.75, 0.0),
-        4: (8.876, 5.001, 2.75, 1.0), 5: (28.502, 17.001, 7.0, 0.0),
-        6: (29.502, 17.251, 7.75, 0.0), 7: (9.126, 6.126, 1.625, 1.0),
-        8: (23.502, 16.126, 7.0, 0.0), 9: (12.376, 5.001, 3.0, 1.0),
-        10: (1.875, 1.0, 0.5, 0.0),
-    },
-}
-OP_SOURCES = ("common.cuh", "measure.cu", "score.cuh", "transcend.cuh")
-
-
-def issue_roofline(progs_list, sm_mhz: float, sms: int = 152):
-    """Time the op work of the populations (list of (programs, N)) needs at the issue and pipe
-    rates; leaves and stack moves are free. None if the operator table is stale."""
-    import hashlib
-    d = os.path.join(ROOT, "paper_2607_06731_gb300", "csrc")
-    h = hashlib.sha256()
-    for name in OP_SOURCES:
-        h.update(name.encode())
-        h.update(open(os.path.join(d, name), "rb").read())
-    if h.hexdigest() != OP_INSTR["sources_sha256"]:
-        return None
-    pipes = ("all", "fma", "alu", "xu")
-    inst = dict.fromkeys(pipes, 0.0)
+def algorithmic_units(progs_list):
+    """Lane operations of each pipe over populations [(programs, N)]."""
+    tot = {"fp32": 0.0, "mufu": 0.0, "alu": 0.0}
     for progs, N in progs_list:
-        counts = np.bincount(progs.ops, minlength=64).astype(np.float64)
-        for op, per in OP_INSTR["per_eval"].items():
-            for k, v in zip(pipes, per):
-                inst[k] += counts[op] * N * v
+        counts = np.bincount(progs.ops, minlength=256).astype(np.float64)
+        for op, (f, m, a) in ALGO_UNITS.items():
+            tot["fp32"] += counts[op] * N * f
+            tot["mufu"] += counts[op] * N * m
+            tot["alu"] += counts[op] * N * a
+    tot["issue"] = tot["fp32"] + tot["mufu"] + tot["alu"]
+    return tot
+
+
+def roofline_time(progs_list, sm_mhz: float, sms: int):
+    """Roofline time of the populations' algorithmic work: the slowest of the FP32, MUFU and
+    ALU pipes and of instruction issue, at the measured SM clock."""
+    units = algorithmic_units(progs_list)
     f = sm_mhz * 1e6
-    t = {k: inst[k] / (OP_INSTR["per_sm_cycle"][k] * 32 * sms * f) for k in pipes}
+    t = {k: units[k] / (LANES_PER_SM_CLK[k] * sms * f) for k in units}
     bind = max(t, key=t.get)
-    return {"seconds": t[bind], "binding": "issue" if bind == "all" else bind + " pipe",
-            "per_pipe_ms": {k: v * 1e3 for k, v in t.items()}}
+    return {"seconds": t[bind], "binding": bind, "per_pipe_ms": {k: v * 1e3 for k, v in t.items()},
+            "lane_ops_per_node_eval": units["issue"] / max(1.0, sum(
+                float(p.lengths.sum(dtype=np.int64)) * N for p, N in progs_list))}
 
 
-def roofline_peak(progs, N, rates):
-    """ALU-issue roofline: the time straight-line compiled code would need for this op mix,
-    every operator at its measured throughput (validity check included), leaves free."""
-    counts = np.bincount(progs.ops, minlength=64).astype(np.float64)
-    t = 0.0
-    for op, r in rates.items():
-        t += counts[op] * N / r
-    return t
+def roofline_line(node_evals, kernel_s, progs_list, sm_mhz, sms, peak_straight=None):
+    rt = roofline_time(progs_list, sm_mhz, sms)
+    peak = node_evals / rt["seconds"] / 1e9
+    achieved = node_evals / kernel_s / 1e9 if kernel_s else None
+    out = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "GPoPs",
+           "frac": achieved / peak if achieved else None, "traffic": None,
+           "peak_basis": (f"algorithmic lane operations per node evaluation (FP32/MUFU/ALU "
+                          f"units per operator, leaves free) at {LANES_PER_SM_CLK} lanes per "
+                          f"SM per clock, {sms} SMs, {sm_mhz:.0f} MHz measured; binding: "
+                          f"{rt['binding']}"),
+           "per_pipe_ms": rt["per_pipe_ms"],
+           "lane_ops_per_node_eval": rt["lane_ops_per_node_eval"],
+           "kernel_ms": kernel_s * 1e3 if kernel_s else None}
+    if peak_straight:
+        out["peak_straight_line_ops"] = peak_straight
+        out["frac_straight_line_ops"] = achieved / peak_straight if achieved else None
+    return out
+
+
+def straight_line_peak(progs, N, rates):
+    """Seconds straight-line compiled code would need for this op mix, every operator at its
+    measured throughput (beagle_measure_op_rates), leaves free."""
+    counts = np.bincount(progs.ops, minlength=256).astype(np.float64)
+    return sum(counts[op] * N / r for op, r in rates.items())
+
+
+# ----------------------------------------------------------------------------- oracle legs
+# The oracle (test infrastructure) runs only here, outside every timed region: the CPU
+# baseline, the reference arm, and the parity gates on a sample of the timed launch's output.
+def _oracle_worker(inp: str, outp: str):
+    """Spawned process: FP32-ops and FP64 oracle results of a program sample."""
+    sys.path.insert(0, ROOT)
+    import oracle
+    oracle.build()
+    z = np.load(inp)
+    res = {}
+    t0 = time.perf_counter()
+    for mode in ("fp32", "fp64"):
+        m, r, f = oracle.score(z["ops"], z["offsets"], z["lengths"], z["consts"], z["X"],
+                               z["y"], mode)
+        res[f"{mode}_mse"], res[f"{mode}_omr2"], res[f"{mode}_flags"] = m, r, f
+    res["seconds"] = np.array(time.perf_counter() - t0)
+    res["threads"] = np.array(oracle.threads())
+    np.savez(outp, **res)
+
+
+class OracleSample:
+    """The oracle on a seeded sample of a population, in a spawned process (started before
+    any GPU work, so that it overlaps the timed runs)."""
+
+    def __init__(self, pr, n: int, seed: int = 11):
+        self.idx = np.sort(np.random.default_rng(seed).choice(pr.programs.P,
+                                                              min(n, pr.programs.P),
+                                                              replace=False))
+        sub = pr.programs.subset(self.idx)
+        self.dir = tempfile.mkdtemp(prefix="beagle_parity_")
+        inp = os.path.join(self.dir, "in.npz")
+        np.savez(inp, ops=sub.ops, offsets=sub.offsets, lengths=sub.lengths, consts=sub.consts,
+                 X=pr.X, y=pr.y)
+        self.out = os.path.join(self.dir, "out.npz")
+        self.proc = mp.get_context("spawn").Process(target=_oracle_worker,
+                                                    args=(inp, self.out))
+        self.t0 = time.perf_counter()
+        self.proc.start()
+
+    def result(self):
+        self.proc.join()
+        wall = time.perf_counter() - self.t0
+        if self.proc.exitcode != 0:
+            shutil.rmtree(self.dir, ignore_errors=True)
+            raise RuntimeError(f"oracle sample process failed ({self.proc.exitcode})")
+        z = dict(np.load(self.out))
+        shutil.rmtree(self.dir, ignore_errors=True)
+        z["wall"] = wall
+        return z
+
+
+def oracle_inline(progs, X, y):
+    import oracle
+    oracle.build()
+    res = {}
+    for mode in ("fp32", "fp64"):
+        m, r, f = oracle.score(progs.ops, progs.offsets, progs.lengths, progs.consts, X, y, mode)
+        res[f"{mode}_mse"], res[f"{mode}_omr2"], res[f"{mode}_flags"] = m, r, f
+    return res
+
+
+def _close(a, b, rel, abs_):
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    inf = np.isinf(a) & np.isinf(b) & (np.sign(a) == np.sign(b))
+    with np.errstate(invalid="ignore"):
+        return (np.abs(a - b) <= np.maximum(rel * np.abs(b), abs_)) | inf
+
+
+def _max_rel(a, b):
+    if len(a) == 0:
+        return None
+    with np.errstate(invalid="ignore", divide="ignore"):
+        r = np.abs(a - b) / np.maximum(np.abs(b), 1e-300)
+    return float(np.max(r))
+
+
+def parity_gates(g32, g64, o):
+    """Gates A, B, C against the oracle without its error bound (a sample too large for the
+    bound's cost). NEAR: the oracle saw a value within 1e-5 of a threshold (1e30, 1e-3), where
+    fp32 and fp64 may decide differently. The strict (well-conditioned) set: valid, not NEAR,
+    and the FP32-ops and FP64 oracle results agree within 1e-6 -- the program's fitness moves
+    by less than 1e-6 under fp32 rounding of every operation, so a device's few-ulp differences
+    cannot move it by 1e-5.
+      flags   GPU flags equal the oracle's on every non-NEAR program (FP32 vs FP32-ops oracle,
+              FP64 vs FP64 oracle)
+      gate A  GPU FP32c vs FP32-ops oracle, |g - o| <= max(1e-5 |o|, 1e-7), strict set
+      gate B  GPU FP32c vs FP64 oracle, same tolerance, strict set
+      gate C  GPU FP64 vs FP64 oracle, |g - o| <= max(1e-12 |o|, 1e-13), strict set"""
+    NEAR, BITS = 256, 7
+    f32, f64 = o["fp32_flags"].astype(np.int64), o["fp64_flags"].astype(np.int64)
+    near = ((f32 | f64) & NEAR) != 0
+    valid = ((f32 & 5) == 0) & ((f64 & 5) == 0)
+    agree = (_close(o["fp32_mse"], o["fp64_mse"], 1e-6, 1e-9) &
+             _close(o["fp32_omr2"], o["fp64_omr2"], 1e-6, 1e-9) &
+             ((f32 & BITS) == (f64 & BITS)))
+    strict = valid & ~near & agree
+    out = {"programs": int(len(f32)), "valid": int(valid.sum()), "near_threshold": int(near.sum()),
+           "strict": int(strict.sum()), "strict_frac": float(strict.mean()) if len(f32) else None}
+    fl32 = int(np.sum(~near & ((g32[2].astype(np.int64) & BITS) != (f32 & BITS))))
+    out["flags_mismatch_fp32"] = fl32
+    ok_all = fl32 == 0
+    for name, g, mse, omr, tol in (("A", g32, "fp32_mse", "fp32_omr2", (1e-5, 1e-7)),
+                                   ("B", g32, "fp64_mse", "fp64_omr2", (1e-5, 1e-7)),
+                                   ("C", g64, "fp64_mse", "fp64_omr2", (1e-12, 1e-13))):
+        if g is None:
+            continue
+        ok = _close(g[0], o[mse], *tol) & _close(g[1], o[omr], *tol)
+        npass = int(np.sum(ok & strict))
+        out[f"gate_{name}"] = {"pass": npass, "of": int(strict.sum()),
+                               "tol_rel": tol[0], "tol_abs": tol[1],
+                               "max_rel_mse": _max_rel(g[0][strict], o[mse][strict]),
+                               "max_rel_one_minus_r2": _max_rel(g[1][strict], o[omr][strict])}
+        ok_all &= npass == int(strict.sum())
+    if g64 is not None:
+        fl64 = int(np.sum(~near & ((g64[2].astype(np.int64) & BITS) != (f64 & BITS))))
+        out["flags_mismatch_fp64"] = fl64
+        ok_all &= fl64 == 0
+    # outside the strict set: how far FP32c lands from the FP64 oracle (conditioning of the
+    # programs themselves, not the aggregation)
+    rest = valid & ~near & ~strict & ((g32[2] & 5) == 0)
+    if rest.any():
+        ok = _close(g32[0], o["fp64_mse"], 1e-5, 1e-7) & _close(g32[1], o["fp64_omr2"], 1e-5, 1e-7)
+        out["outside_strict_within_1e-5_of_fp64"] = float(np.mean(ok[rest]))
+    out["all_pass"] = bool(ok_all)
+    return out
 
 
 def cpu_baseline(pr, seconds: float, threads: int = 0):
@@ -236,61 +363,17 @@ def cpu_baseline(pr, seconds: float, threads: int = 0):
     return out
 
 
-def aggregation_error(beagle, synth, progs, pr, ds, fp32, n=2000):
-    """Relative error of the FP32c fitness against plain fp64 sums of the same per-case fp32
-    outputs, over a seeded sample of valid, non-degenerate programs."""
-    import torch
-    rng = np.random.default_rng(7)
-    idx = np.sort(rng.choice(progs.P, min(n, progs.P), replace=False))
-    dp = beagle.DevicePrograms(progs.subset(idx))
-    outs, _ = beagle.eval_programs(dp, ds)
-    f = outs.double().cpu().numpy()
-    torch.cuda.synchronize()
-    y = pr.y.astype(np.float64)
-    with np.errstate(invalid="ignore", divide="ignore", over="ignore"):   # invalid programs
-        mse = ((f - y) ** 2).mean(axis=1)
-        fc = f - f.mean(axis=1, keepdims=True)
-        yc = y - y.mean()
-        r = (fc * yc).sum(axis=1) / np.sqrt((fc * fc).sum(axis=1) * (yc * yc).sum())
-        omr = 1.0 - r * r
-    ok = (fp32[2][idx] == 0) & np.isfinite(mse) & np.isfinite(omr)
-    out = {"programs_compared": int(ok.sum())}
-    for name, ref, got in (("mse", mse, fp32[0][idx]), ("one_minus_r2", omr, fp32[1][idx])):
-        a, b = got[ok], ref[ok]
-        err = np.abs(a - b)
-        rel = err / np.maximum(np.abs(b), 1e-300)
-        out[name] = {"frac_within_1e-5": float(np.mean(err <= np.maximum(1e-5 * np.abs(b),
-                                                                           1e-7))),
-                     "max_rel": float(rel.max()) if len(rel) else None,
-                     "median_rel": float(np.median(rel)) if len(rel) else None}
-    return out
-
-
-def max_over_ranks(value: float, dist, device: str) -> float:
-    """The slowest rank's time (the job ends when every rank has finished); identity on 1."""
-    if dist is None:
-        return value
-    import torch
-    t = torch.tensor([value], dtype=torch.float64, device=device)
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    return float(t.item())
-
-
-def whole_job_gpops(node_evals_per_rank_step: int, steps: int, world: int, ms: float) -> float:
-    """Weak scaling: every rank scores its own population of the same size each step."""
-    return node_evals_per_rank_step * steps * world / (ms / 1e3) / 1e9
-
-
 def run_reference(args, rank, world):
-    """The oracle timed as the reference arm: each step scores a bounded seeded sample."""
+    """The oracle timed as the reference arm on the headline workload: each step scores a
+    bounded seeded sample of the precision population at the full case count."""
     if rank != 0:
         return 0
     from paper_2607_06731_gb300 import synth
     import oracle
     oracle.build()
-    pr = synth.make_c2(P=args.P)
+    pr = synth.make_c3(P=args.P or 50_000)
     rng = np.random.default_rng(99)
-    n = 200
+    n = 16
     sub = pr.programs.subset(rng.choice(pr.programs.P, n, replace=False))
     t0 = time.perf_counter()
     oracle.score_programs(sub, pr.X, pr.y, "fp64")
@@ -313,7 +396,7 @@ def run_reference(args, rank, world):
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": tot / args.steps * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "P": pr.programs.P, "N": pr.N, "d": pr.d,
+            "config": {"workload": C3_DESC, "P": pr.programs.P, "N": pr.N, "d": pr.d,
                        "sample_programs": n},
             "cpu_baseline": {"value": value, "unit": "GPoPs", "cores": oracle.threads(),
                              "kind": "oracle", "sample": sample},
@@ -323,13 +406,17 @@ def run_reference(args, rank, world):
     return 0
 
 
-# ----------------------------------------------------------------------------- c3 / c4 / c5
-def _timed_steps(step, steps, warmup, stream, flush):
+# ----------------------------------------------------------------------------- GPU legs
+def timed_steps(step, steps, warmup, stream, flush, barrier=None):
+    """W untimed warm-up steps, then K steps each between CUDA events on the launching
+    stream, L2 flushed before every step outside the events. Returns per-step ms."""
     import torch
-    for _ in range(max(3, warmup)):
+    for _ in range(warmup):
         flush.zero_()
         step()
     torch.cuda.synchronize()
+    if barrier:
+        barrier()
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
            for _ in range(steps)]
     for a, b in evs:
@@ -338,6 +425,8 @@ def _timed_steps(step, steps, warmup, stream, flush):
         step()
         b.record(stream)
     torch.cuda.synchronize()
+    if barrier:
+        barrier()
     return [a.elapsed_time(b) for a, b in evs]
 
 
@@ -346,93 +435,106 @@ def _pctl(v, q):
     return v[min(len(v) - 1, int(round(q * (len(v) - 1))))] if v else None
 
 
-def run_other_workload(args, rank, world, local):
-    """Secondary workloads, each printing its own JSON line (config.workload names it)."""
-    import __graft_entry__
-    __graft_entry__.build()
+def e2e_host(beagle, progs, ds, stream, steps):
+    """GPoPs end to end through beagle_score_host: programs from pinned host memory to the
+    device and the fitness records back, inside the timed region (the dataset is resident)."""
     import torch
-    from paper_2607_06731_gb300 import beagle, synth
-    torch.cuda.set_device(local)
-    stream = torch.cuda.current_stream()
-    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
-    rates = beagle.measure_op_rates(1.0, stream=stream)
-    clocks = Clocks(local)
-    base = {"metric": METRIC, "unit": "GPoPs", "n_gpus": world, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic"}
-    if args.workload in ("c1", "c3"):
-        line = _run_c3(args, beagle, synth, torch, stream, flush, rates, clocks, args.workload)
-    elif args.workload == "c4":
-        line = _run_c4(args, beagle, synth, torch, stream, flush, rates, clocks)
-    else:
-        line = _run_c5(args, beagle, synth, torch, stream, rates, clocks)
-    if rank == 0:
-        print(json.dumps({**base, **line}), flush=True)
-    return 0
+    from paper_2607_06731_gb300 import synth
+    pinned = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in
+              (progs.ops, progs.offsets, progs.lengths, progs.consts)]
+    hp = synth.Programs(*(t.numpy() for t in pinned))
+    hout = torch.empty(progs.P * 3, dtype=torch.float64).pin_memory()
+    hout_np = hout.numpy().view(beagle.FITNESS_DTYPE)
+    beagle.score_host(hp, ds, out=hout_np, stream=stream)
+    ts = []
+    for _ in range(steps):
+        t0 = time.perf_counter()
+        beagle.score_host(hp, ds, out=hout_np, stream=stream)
+        ts.append(time.perf_counter() - t0)
+    h2d = hp.ops.nbytes + hp.offsets.nbytes + hp.lengths.nbytes + hp.consts.nbytes
+    return {"seconds": statistics.median(ts), "h2d": int(h2d),
+            "d2h": int(progs.P * beagle.FITNESS_DTYPE.itemsize)}
 
 
-C1_DESC = ("c1-small-1024: P=1024 programs, length U{8..32}, d=2, N=1024 cases, X~U[-3,3], "
-           "y = x0 sin(x1) + x0^2/2")
-C3_DESC = ("c3-precision-1m: P=50000 programs, length U{16..64}, d=10, N=1000000 cases, "
-           "X~N(0,1), y RMS 1e3 + N(0,1)")
-
-
-def _run_c3(args, beagle, synth, torch, stream, flush, rates, clocks, which="c3"):
-    """One population on one dataset, FP32-compensated and plain FP64 paths, the error of the
-    first against the second: the precision workload (50,000 programs, length U{16..64}, on
-    1e6 cases, d = 10, y of RMS 1e3) or the small oracle-sized one (c1)."""
-    pr = synth.make_c3() if which == "c3" else synth.make_c1()
+def score_population(beagle, torch, pr, stream, flush, steps, warmup, clocks=None,
+                     fp64_steps=1, barrier=None, autotune=False):
+    """Time one population: FP32c steps (kernel time too), then the FP64 path."""
     ds = beagle.Dataset(pr.X, pr.y)
     dp = beagle.DevicePrograms(pr.programs)
     out = torch.empty((dp.P, 3), dtype=torch.float64, device="cuda")
-    tuned = beagle.autotune([(dp, ds, out)])[0] if args.autotune else None
-    clocks.start()
+    tuned = beagle.autotune([(dp, ds, out)])[0] if autotune else None
+    if clocks:
+        clocks.start()
     beagle.kernel_timing(True)
     beagle.kernel_time()
-    ms = _timed_steps(lambda: beagle.score_programs(dp, ds, out=out, stream=stream),
-                      args.steps, args.warmup, stream, flush)
-    clk = clocks.stop()
+    ms = timed_steps(lambda: beagle.score_programs(dp, ds, out=out, stream=stream),
+                     steps, warmup, stream, flush, barrier)
+    clk = clocks.stop() if clocks else None
     beagle.kernel_timing(False)
     kern_ms, kern_n = beagle.kernel_time()
-    f32 = beagle.unpack_fitness(out)
-    ms64 = _timed_steps(lambda: beagle.score_programs(dp, ds, out=out, precision="fp64",
-                                                      stream=stream),
-                        max(1, args.fp64_steps), 0, stream, flush)
-    f64 = beagle.unpack_fitness(out)
-    ok = ((f32[2] & 5) == 0) & ((f64[2] & 5) == 0)
-    err = {}
+    g32 = beagle.unpack_fitness(out)
+    g64, ms64 = None, None
+    if fp64_steps > 0:
+        ms64 = timed_steps(lambda: beagle.score_programs(dp, ds, out=out, precision="fp64",
+                                                         stream=stream),
+                           fp64_steps, 0, stream, flush)
+        g64 = beagle.unpack_fitness(out)
+    # kernel time of the timed steps only (warm-up launches were timed too: drop them)
+    kern_avg = kern_ms / max(kern_n, 1) / 1e3
+    return {"ds": ds, "dp": dp, "ms": ms, "ms64": ms64, "g32": g32, "g64": g64, "clk": clk,
+            "kernel_s": kern_avg, "tuned": tuned}
+
+
+def fp32_vs_fp64_path(g32, g64):
+    ok = ((g32[2] & 5) == 0) & ((g64[2] & 5) == 0)
+    out = {"programs_compared": int(ok.sum())}
     for k, name in ((0, "mse"), (1, "one_minus_r2")):
-        a, b = f32[k][ok], f64[k][ok]
-        rel = np.abs(a - b) / np.maximum(np.abs(b), 1e-300)
-        err[name] = {"frac_within_1e-5": float(np.mean(np.abs(a - b) <=
-                                                        np.maximum(1e-5 * np.abs(b), 1e-7))),
-                     "median_rel": float(np.median(rel)), "max_rel": float(rel.max())}
+        a, b = g32[k][ok], g64[k][ok]
+        out[name] = {"frac_within_1e-5": float(np.mean(_close(a, b, 1e-5, 1e-7))) if ok.any()
+                     else None, "max_rel": _max_rel(a, b)}
+    return out
+
+
+def sub_c1(beagle, synth, torch, stream, flush, args, sm_mhz, sms, rates):
+    pr = synth.make_c1()
+    r = score_population(beagle, torch, pr, stream, flush, max(200, args.steps),
+                         max(3, args.warmup), fp64_steps=5)
+    o = oracle_inline(pr.programs, pr.X, pr.y)
     ev = pr.node_evals
-    kern_s = kern_ms / max(kern_n, 1) / 1e3
-    peak_straight = ev / roofline_peak(pr.programs, pr.N, rates) / 1e9
-    issue = issue_roofline([(pr.programs, pr.N)], clk["sm_mhz"] or 2070.0)
-    peak = ev / issue["seconds"] / 1e9 if issue else peak_straight
-    return {"value": ev * len(ms) / (sum(ms) / 1e3) / 1e9, "steps": len(ms),
-            "warmup": max(3, args.warmup), "ms_per_step": statistics.mean(ms),
-            "p50_ms": _pctl(ms, 0.5), "p99_ms": _pctl(ms, 0.99),
-            "config": {"workload": C3_DESC if which == "c3" else C1_DESC,
-                       "P": dp.P, "N": pr.N, "d": pr.d, "node_evals_per_step": ev,
-                       "l2": "256 MiB flush before every step", "autotuned": tuned},
-            "fp64": {"value": ev / (statistics.median(ms64) / 1e3) / 1e9, "unit": "GPoPs",
-                     "ms_per_step": statistics.median(ms64)},
-            "fp32c_error_vs_fp64_path": {"programs_compared": int(ok.sum()), **err},
-            "roofline": {"bound": "alu", "achieved": ev / kern_s / 1e9, "peak": peak,
-                         "unit": "GPoPs", "frac": ev / kern_s / 1e9 / peak, "traffic": None,
-                         "peak_basis": ("issue roofline, binding: " + issue["binding"])
-                                       if issue else "straight-line per-op throughput",
-                         "peak_straight_line_ops": peak_straight},
-            "cpu_baseline": cpu_baseline(pr, args.cpu_seconds),
-            "gpu_launches": LAUNCHES_PER_CALL * len(ms), "clocks": clk}
+    out = {"workload": C1_DESC, "value": ev * len(r["ms"]) / (sum(r["ms"]) / 1e3) / 1e9,
+           "unit": "GPoPs", "ms_per_step": statistics.mean(r["ms"]),
+           "p50_ms": _pctl(r["ms"], 0.5), "p99_ms": _pctl(r["ms"], 0.99),
+           "fp64": {"value": ev / (statistics.median(r["ms64"]) / 1e3) / 1e9},
+           "roofline": roofline_line(ev, r["kernel_s"], [(pr.programs, pr.N)], sm_mhz, sms,
+                                     ev / straight_line_peak(pr.programs, pr.N, rates) / 1e9),
+           "parity_full_population": parity_gates(r["g32"], r["g64"], o)}
+    r["ds"].release()
+    return out
 
 
-def _run_c4(args, beagle, synth, torch, stream, flush, rates, clocks):
-    """64 ragged populations (P log-U[1e3, 2e5], L U{4..256}, N log-U[256, 1e5], d U{1..10}),
-    each with its own resident dataset, scored in one graph-captured persistent batch; the
-    same populations scored one call each for comparison."""
+def sub_c2(beagle, synth, torch, stream, flush, args, sm_mhz, sms, rates):
+    pr = synth.make_c2()
+    r = score_population(beagle, torch, pr, stream, flush, max(100, args.steps),
+                         max(3, args.warmup), fp64_steps=2)
+    idx = np.sort(np.random.default_rng(12).choice(pr.programs.P, 2000, replace=False))
+    o = oracle_inline(pr.programs.subset(idx), pr.X, pr.y)
+    sel = lambda g: tuple(a[idx] for a in g)  # noqa: E731
+    e2e = e2e_host(beagle, pr.programs, r["ds"], stream, 5)
+    ev = pr.node_evals
+    out = {"workload": C2_DESC, "value": ev * len(r["ms"]) / (sum(r["ms"]) / 1e3) / 1e9,
+           "unit": "GPoPs", "ms_per_step": statistics.mean(r["ms"]),
+           "p50_ms": _pctl(r["ms"], 0.5), "p99_ms": _pctl(r["ms"], 0.99),
+           "fp64": {"value": ev / (statistics.median(r["ms64"]) / 1e3) / 1e9},
+           "e2e": {"value": ev / e2e["seconds"] / 1e9, "unit": "GPoPs",
+                   "h2d_bytes_per_step": e2e["h2d"], "d2h_bytes_per_step": e2e["d2h"]},
+           "roofline": roofline_line(ev, r["kernel_s"], [(pr.programs, pr.N)], sm_mhz, sms,
+                                     ev / straight_line_peak(pr.programs, pr.N, rates) / 1e9),
+           "parity_sample": parity_gates(sel(r["g32"]), sel(r["g64"]), o)}
+    r["ds"].release()
+    return out
+
+
+def sub_c4(beagle, synth, torch, stream, flush, args, sm_mhz, sms, steps=None, clocks=None):
     pops = synth.make_c4()
     items = []
     for pr in pops:
@@ -440,13 +542,17 @@ def _run_c4(args, beagle, synth, torch, stream, flush, rates, clocks):
         dp = beagle.DevicePrograms(pr.programs)
         items.append((dp, ds, torch.empty((dp.P, 3), dtype=torch.float64, device="cuda")))
     ev = sum(pr.node_evals for pr in pops)
-    tuned = beagle.autotune(items)[0] if args.autotune else None
     plan = beagle.BatchPlan(items)
-    clocks.start()
-    ms = _timed_steps(lambda: plan.launch(stream), args.steps, args.warmup, stream, flush)
-    clk = clocks.stop()
-    # kernel time of the scoring kernel: the same batch launched uncaptured (graph replays
-    # bypass the library's launch hooks)
+    k = steps or max(3, min(10, args.steps))
+    warm = max(3, min(args.warmup, 5))
+    if clocks:
+        clocks.start()
+    ms = timed_steps(lambda: plan.launch(stream), k, warm, stream, flush)
+    clk = clocks.stop() if clocks else None
+    if clk and clk["sm_mhz"]:
+        sm_mhz = clk["sm_mhz"]
+    # scoring-kernel time: the same batch launched uncaptured (graph replays bypass the
+    # library's launch hooks)
     beagle.kernel_timing(True)
     beagle.kernel_time()
     for _ in range(2):
@@ -459,40 +565,187 @@ def _run_c4(args, beagle, synth, torch, stream, flush, rates, clocks):
     def one_by_one():
         for dp, ds, out in items:
             beagle.score_programs(dp, ds, out=out, stream=stream)
-    ms1 = _timed_steps(one_by_one, max(1, min(3, args.steps)), 1, stream, flush)
-    t_roof = sum(roofline_peak(pr.programs, pr.N, rates) for pr in pops)
-    issue = issue_roofline([(pr.programs, pr.N) for pr in pops], clk["sm_mhz"] or 2070.0)
-    if issue:
-        t_roof = issue["seconds"]
-    # scoring launches per batch (the batch is cut by input width), each with its length
-    # order and finalize kernels
-    launches_per_plan = (kern_n // 2) * LAUNCHES_PER_CALL
-    kern_s = kern_ms / 1e3 / 2                   # scoring-kernel time per batch (all launches)
-    big = max(pops, key=lambda p: p.node_evals)
-    return {"value": ev * len(ms) / (sum(ms) / 1e3) / 1e9, "steps": len(ms),
-            "warmup": max(3, args.warmup), "ms_per_step": statistics.mean(ms),
-            "p50_ms": _pctl(ms, 0.5), "p99_ms": _pctl(ms, 0.99),
-            "config": {"workload": "c4-ragged-64: 64 populations, P log-U[1e3,2e5], "
-                                   "L U{4..256}, N log-U[256,1e5], d U{1..10}, one dataset "
-                                   "each; one graph-captured batch per step",
-                       "populations": len(pops), "programs": int(sum(p.programs.P for p in pops)),
-                       "node_evals_per_step": ev, "autotuned": tuned,
-                       "l2": "256 MiB flush before every step"},
+    ms1 = timed_steps(one_by_one, 2, 1, stream, flush)
+    plan.destroy()
+    for _, ds, _ in items:
+        ds.release()
+    kern_s = kern_ms / 1e3 / 2
+    return {"workload": C4_DESC, "value": ev * len(ms) / (sum(ms) / 1e3) / 1e9, "unit": "GPoPs",
+            "ms_per_step": statistics.mean(ms), "steps": len(ms), "warmup": warm, "clocks": clk,
+            "populations": len(pops), "programs": int(sum(p.programs.P for p in pops)),
+            "node_evals_per_step": ev, "scoring_launches_per_step": kern_n // 2,
             "one_call_per_population": {"value": ev / (statistics.median(ms1) / 1e3) / 1e9,
-                                        "unit": "GPoPs", "ms_per_step": statistics.median(ms1)},
-            "roofline": {"bound": "alu", "achieved": ev / kern_s / 1e9 if kern_s else None,
-                         "peak": ev / t_roof / 1e9, "unit": "GPoPs",
-                         "frac": (ev / kern_s / 1e9) / (ev / t_roof / 1e9) if kern_s else None,
-                         "traffic": None, "kernel_launches_timed": kern_n,
-                         "peak_basis": ("issue roofline, binding: " + issue["binding"])
-                                       if issue else "straight-line per-op throughput"},
-            "cpu_baseline": cpu_baseline(big, args.cpu_seconds),
-            "gpu_launches": launches_per_plan * len(ms), "clocks": clk}
+                                        "unit": "GPoPs"},
+            "roofline": roofline_line(ev, kern_s, [(pr.programs, pr.N) for pr in pops],
+                                      sm_mhz or 2070.0, sms)}
 
 
-def _run_c5(args, beagle, synth, torch, stream, rates, clocks):
+def run_headline(args, rank, world, local):
+    """The precision workload (50,000 programs x 10^6 cases): FP32c timed, FP64 path, end to
+    end through the host-buffer call, the oracle's gates on a 10,000-program sample of the
+    timed launch, the CPU baseline, and compact c1/c2/c4 sub-lines."""
+    from paper_2607_06731_gb300 import synth
+    pr = synth.make_c3(seed=3 + rank, P=args.P or 50_000)
+    # the oracle sample runs in a spawned process while the GPU works
+    osample = OracleSample(pr, args.parity_sample) if (rank == 0 and args.parity_sample) else None
+
+    import __graft_entry__
+    __graft_entry__.build()
+    import torch
+    from paper_2607_06731_gb300 import beagle
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    clocks = Clocks(local)
+    warm = max(3, args.warmup)
+    r = score_population(beagle, torch, pr, stream, flush, args.steps, warm, clocks=clocks,
+                         fp64_steps=max(1, args.fp64_steps), barrier=barrier,
+                         autotune=args.autotune)
+    tot_ms = max_over_ranks(sum(r["ms"]), dist, "cuda")
+    clk = r["clk"]
+    sm_mhz = clk["sm_mhz"] or 2070.0
+    e2e = e2e_host(beagle, pr.programs, r["ds"], stream, max(1, args.e2e_steps))
+    rates = beagle.measure_op_rates(1.0, stream=stream)
+    ev = pr.node_evals
+    subs = {}
+    if rank == 0 and not args.no_sub:
+        subs["c1"] = sub_c1(beagle, synth, torch, stream, flush, args, sm_mhz, sms, rates)
+        subs["c2"] = sub_c2(beagle, synth, torch, stream, flush, args, sm_mhz, sms, rates)
+        subs["c4"] = sub_c4(beagle, synth, torch, stream, flush, args, sm_mhz, sms)
+        subs["c4"].pop("clocks", None)
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return 0
+    parity = None
+    if osample is not None:
+        o = osample.result()
+        sel = lambda g: tuple(a[osample.idx] for a in g)  # noqa: E731
+        parity = parity_gates(sel(r["g32"]), sel(r["g64"]), o)
+        parity["sample"] = (f"{len(osample.idx)} of {pr.programs.P} programs (seeded) of the "
+                            f"timed launch, all {pr.N} cases")
+        parity["oracle_seconds"] = float(o["seconds"])
+        parity["oracle_threads"] = int(o["threads"])
+    cpu = cpu_baseline(pr, args.cpu_seconds)
+    ms = r["ms"]
+    line = {
+        "metric": METRIC,
+        "value": ev * args.steps * world / (tot_ms / 1e3) / 1e9,
+        "unit": "GPoPs", "n_gpus": world, "steps": args.steps, "warmup": warm,
+        "ms_per_step": tot_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": C3_DESC, "P": pr.programs.P, "N": pr.N, "d": pr.d,
+                   "tokens": pr.programs.tokens, "node_evals_per_step": ev,
+                   "precision": "fp32-compensated (fp32 ops, compensated fp32 tile sums, fp64 "
+                                "cross-tile merge)",
+                   "l2": "flushed before every timed step (256 MiB write, outside events)",
+                   "parallelism": f"replicas x{world} (independent populations)",
+                   "autotuned": r["tuned"]},
+        "p50_ms": _pctl(ms, 0.5), "p99_ms": _pctl(ms, 0.99),
+        "fp64": {"value": ev / (statistics.median(r["ms64"]) / 1e3) / 1e9, "unit": "GPoPs",
+                 "ms_per_step": statistics.median(r["ms64"])},
+        "fp32c_vs_fp64_speedup": statistics.median(r["ms64"]) / statistics.median(ms),
+        "fp32c_vs_fp64_path": fp32_vs_fp64_path(r["g32"], r["g64"]),
+        "parity": parity,
+        "roofline": roofline_line(ev, r["kernel_s"], [(pr.programs, pr.N)], sm_mhz, sms,
+                                  ev / straight_line_peak(pr.programs, pr.N, rates) / 1e9),
+        "cpu_baseline": cpu,
+        "e2e": {"value": ev / e2e["seconds"] / 1e9, "unit": "GPoPs",
+                "h2d_bytes_per_step": e2e["h2d"], "d2h_bytes_per_step": e2e["d2h"]},
+        "gpu_launches": LAUNCHES_PER_CALL * args.steps,
+        "clocks": clk,
+        "workloads": subs,
+    }
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def max_over_ranks(value: float, dist, device: str) -> float:
+    """The slowest rank's time (the job ends when every rank has finished); identity on 1."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_gpops(node_evals_per_rank_step: int, steps: int, world: int, ms: float) -> float:
+    """Weak scaling: every rank scores its own population of the same size each step."""
+    return node_evals_per_rank_step * steps * world / (ms / 1e3) / 1e9
+
+
+def run_single(args, rank, world, local):
+    """One workload on its own line (config.workload names it)."""
+    import __graft_entry__
+    __graft_entry__.build()
+    import torch
+    from paper_2607_06731_gb300 import beagle, synth
+    torch.cuda.set_device(local)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    rates = beagle.measure_op_rates(1.0, stream=stream)
+    base = {"metric": METRIC, "unit": "GPoPs", "n_gpus": world, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic"}
+    clocks = Clocks(local)
+    if args.workload == "c5":
+        line = run_c5(args, beagle, synth, torch, clocks)
+    elif args.workload == "c4":
+        sub = sub_c4(beagle, synth, torch, stream, flush, args, None, sms, steps=args.steps,
+                     clocks=clocks)
+        clk = sub.pop("clocks")
+        line = {"value": sub.pop("value"), "steps": sub.pop("steps"),
+                "warmup": sub.pop("warmup"), "ms_per_step": sub.pop("ms_per_step"),
+                "config": {"workload": sub.pop("workload"), "l2": "256 MiB flush per step"},
+                **sub, "gpu_launches": LAUNCHES_PER_CALL * sub["scoring_launches_per_step"] *
+                args.steps, "clocks": clk}
+    else:
+        maker = {"c1": synth.make_c1, "c2": synth.make_c2, "c3": synth.make_c3}[args.workload]
+        pr = maker(P=args.P) if args.P else maker()
+        r = score_population(beagle, torch, pr, stream, flush, args.steps, max(3, args.warmup),
+                             clocks=clocks, fp64_steps=args.fp64_steps, autotune=args.autotune)
+        ev = pr.node_evals
+        sm_mhz = r["clk"]["sm_mhz"] or 2070.0
+        desc = {"c1": C1_DESC, "c2": C2_DESC, "c3": C3_DESC}[args.workload]
+        e2e = e2e_host(beagle, pr.programs, r["ds"], stream, max(1, args.e2e_steps))
+        line = {"value": ev * len(r["ms"]) / (sum(r["ms"]) / 1e3) / 1e9, "steps": args.steps,
+                "warmup": max(3, args.warmup), "ms_per_step": statistics.mean(r["ms"]),
+                "p50_ms": _pctl(r["ms"], 0.5), "p99_ms": _pctl(r["ms"], 0.99),
+                "config": {"workload": desc, "P": pr.programs.P, "N": pr.N, "d": pr.d,
+                           "node_evals_per_step": ev, "autotuned": r["tuned"],
+                           "l2": "256 MiB flush before every step"},
+                "fp64": ({"value": ev / (statistics.median(r["ms64"]) / 1e3) / 1e9}
+                         if r["ms64"] else None),
+                "fp32c_vs_fp64_path": fp32_vs_fp64_path(r["g32"], r["g64"]) if r["g64"] else None,
+                "roofline": roofline_line(ev, r["kernel_s"], [(pr.programs, pr.N)], sm_mhz, sms,
+                                          ev / straight_line_peak(pr.programs, pr.N, rates) / 1e9),
+                "e2e": {"value": ev / e2e["seconds"] / 1e9, "unit": "GPoPs",
+                        "h2d_bytes_per_step": e2e["h2d"], "d2h_bytes_per_step": e2e["d2h"]},
+                "cpu_baseline": cpu_baseline(pr, args.cpu_seconds),
+                "gpu_launches": LAUNCHES_PER_CALL * args.steps, "clocks": r["clk"]}
+        r["ds"].release()
+    if rank == 0:
+        print(json.dumps({**base, **line}), flush=True)
+    return 0
+
+
+def run_c5(args, beagle, synth, torch, clocks):
     """Serving: 16 evolutionary runs with resident datasets submit generations (P log-U[1e4,
-    5e5], L U{8..200}) to one server; first at once (capacity), then as Poisson arrivals at
+    5e5], L U{8..200}) to one server; first all at once (capacity), then as Poisson arrivals at
     0.5x, 0.9x and 1.2x of that capacity. Reports GPoPs and p50 / p99 latency per level.
     Request populations are slices of one 100k-program population per input count d (cycled
     where a request asks for more), generated before timing."""
@@ -507,7 +760,7 @@ def _run_c5(args, beagle, synth, torch, stream, rates, clocks):
 
     def make_requests(n):
         reqs = []
-        for k in range(n):
+        for _ in range(n):
             run = int(rng.integers(len(runs)))
             pool = pools[runs[run]["d"]]
             P = int(np.exp(rng.uniform(np.log(1e4), np.log(5e5))))
@@ -518,9 +771,7 @@ def _run_c5(args, beagle, synth, torch, stream, rates, clocks):
 
     def serve(reqs, rate_rps):
         srv = beagle.Server()
-        res = []
         t0 = time.perf_counter()
-
         tickets = []
         arr = np.cumsum(rng.exponential(1.0 / rate_rps, len(reqs))) if rate_rps else None
         for k, (run, progs, _) in enumerate(reqs):
@@ -530,14 +781,13 @@ def _run_c5(args, beagle, synth, torch, stream, rates, clocks):
                     time.sleep(dt)
             tickets.append(srv.submit(progs, dsets[run]))
         for t in tickets:        # latency is measured by the server (submit to result)
-            res.append(srv.wait(t))
+            srv.wait(t)
         wall = time.perf_counter() - t0
         st = srv.stats()
         srv.destroy()
         return wall, st
 
-    warm = make_requests(4)
-    serve(warm, 0)
+    serve(make_requests(4), 0)
     reqs = make_requests(args.requests)
     ev = sum(r[2] for r in reqs)
     clocks.start()
@@ -545,16 +795,17 @@ def _run_c5(args, beagle, synth, torch, stream, rates, clocks):
     cap_rps = len(reqs) / wall
     levels = {}
     for f in (0.5, 0.9, 1.2):
-        reqs_f = make_requests(args.requests)
-        w, s2 = serve(reqs_f, f * cap_rps)
+        w, s2 = serve(reqs, f * cap_rps)
         levels[f"{f}x"] = {"offered_rps": f * cap_rps, "gpops": s2["gpops"],
                            "p50_ms": s2["p50_us"] / 1e3, "p99_ms": s2["p99_us"] / 1e3,
                            "max_ms": s2["max_us"] / 1e3, "launches": s2["launches"],
                            "peak_gb": s2["peak_bytes"] / 1e9}
     clk = clocks.stop()
-    ex = make_requests(1)[0]
+    ex = reqs[0]
     pr = synth.Problem("c5-sample", ex[1], runs[ex[0]]["X"], runs[ex[0]]["y"], {})
-    return {"value": st["gpops"], "steps": len(reqs), "warmup": len(warm),
+    for ds in dsets:
+        ds.release()
+    return {"value": st["gpops"], "steps": len(reqs), "warmup": 4,
             "ms_per_step": wall / len(reqs) * 1e3,
             "p50_ms": st["p50_us"] / 1e3, "p99_ms": st["p99_us"] / 1e3,
             "config": {"workload": "c5-serving: 16 runs with resident datasets (N log-U[512,"
@@ -580,175 +831,9 @@ def main():
     rank, world, local = dist_env()
     if args.impl == "reference":
         return run_reference(args, rank, world)
-
-    if args.workload != "c2":
-        return run_other_workload(args, rank, world, local)
-
-    import __graft_entry__
-    __graft_entry__.build()
-    import torch
-    from paper_2607_06731_gb300 import beagle, synth
-
-    torch.cuda.set_device(local)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-
-    def barrier():
-        if dist is not None:
-            dist.barrier()
-        torch.cuda.synchronize()
-
-    pr = synth.make_c2(seed=2 + rank, P=args.P)
-    progs = pr.programs
-    node_evals = pr.node_evals
-    ds = beagle.Dataset(pr.X, pr.y)
-    dp = beagle.DevicePrograms(progs)
-    out = torch.empty((progs.P, 3), dtype=torch.float64, device="cuda")
-    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
-    stream = torch.cuda.current_stream()
-
-    def step(precision="fp32c"):
-        beagle.score_programs(dp, ds, out=out, precision=precision, stream=stream)
-
-    # W untimed warm-up steps, continued until a second of work has run: the first second in a
-    # fresh process runs a few per cent slower while the clocks settle.
-    warm = 0
-    t_warm = time.perf_counter()
-    while warm < max(3, args.warmup) or time.perf_counter() - t_warm < 1.0:
-        flush.zero_()
-        step()
-        warm += 1
-        if warm % 16 == 0:
-            torch.cuda.synchronize()
-    barrier()
-    clocks = Clocks(local)
-    clocks.start()
-    beagle.kernel_timing(True)
-    beagle.kernel_time()
-    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-           for _ in range(args.steps)]
-    barrier()
-    for a, b in evs:
-        flush.zero_()
-        a.record(stream)
-        step()
-        b.record(stream)
-    barrier()
-    clk = clocks.stop()
-    beagle.kernel_timing(False)
-    kern_ms, kern_launches = beagle.kernel_time()
-    step_ms = [a.elapsed_time(b) for a, b in evs]
-    tot_ms = sum(step_ms)
-    tot_ms = max_over_ranks(tot_ms, dist, "cuda")
-    fp32 = beagle.unpack_fitness(out)
-
-    # plain FP64 path (same workload, fewer steps)
-    step("fp64")
-    torch.cuda.synchronize()
-    f64_ms = []
-    for _ in range(args.fp64_steps):
-        flush.zero_()
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        step("fp64")
-        b.record(stream)
-        torch.cuda.synchronize()
-        f64_ms.append(a.elapsed_time(b))
-    fp64 = beagle.unpack_fitness(out)
-
-    # relative error of FP32c against the FP64 path (valid programs in both)
-    ok = ((fp32[2] & 5) == 0) & ((fp64[2] & 5) == 0)
-    rel = np.abs(fp32[0][ok] - fp64[0][ok]) / np.maximum(np.abs(fp64[0][ok]), 1e-300)
-    within = (np.abs(fp32[0][ok] - fp64[0][ok]) <= np.maximum(1e-5 * np.abs(fp64[0][ok]), 1e-7))
-
-    # The aggregation alone: the FP32c path's fitness against plain fp64 sums (numpy) of the
-    # same per-case fp32 outputs (beagle_eval), on a seeded sample of programs.
-    agg = aggregation_error(beagle, synth, progs, pr, ds, fp32)
-
-    # end to end through the host-buffer C-ABI call (copies inside the timed region)
-    host = synth.Programs(*(np.ascontiguousarray(a) for a in
-                            (progs.ops, progs.offsets, progs.lengths, progs.consts)))
-    pinned = [torch.from_numpy(a).pin_memory() for a in
-              (host.ops, host.offsets, host.lengths, host.consts)]
-    hp = synth.Programs(*(t.numpy() for t in pinned))
-    hout = torch.empty(progs.P * 3, dtype=torch.float64).pin_memory()
-    hout_np = hout.numpy().view(beagle.FITNESS_DTYPE)
-    beagle.score_host(hp, ds, out=hout_np, stream=stream)
-    e2e_s = []
-    for _ in range(args.e2e_steps):
-        t0 = time.perf_counter()
-        beagle.score_host(hp, ds, out=hout_np, stream=stream)
-        e2e_s.append(time.perf_counter() - t0)
-    h2d = hp.ops.nbytes + hp.offsets.nbytes + hp.lengths.nbytes + hp.consts.nbytes
-    d2h = progs.P * beagle.FITNESS_DTYPE.itemsize
-
-    rates = beagle.measure_op_rates(1.0, stream=stream)
-    t_straight = roofline_peak(progs, pr.N, rates)
-    kern_avg_s = kern_ms / max(kern_launches, 1) / 1e3
-    achieved = node_evals / kern_avg_s / 1e9
-    issue = issue_roofline([(progs, pr.N)], clk["sm_mhz"] or 2070.0)
-    peak_straight = node_evals / t_straight / 1e9
-    peak = node_evals / issue["seconds"] / 1e9 if issue else peak_straight
-
-    if rank != 0:
-        return 0
-    cpu = cpu_baseline(pr, args.cpu_seconds)
-    srt = sorted(step_ms)
-    line = {
-        "metric": METRIC,
-        "value": whole_job_gpops(node_evals, args.steps, world, tot_ms),
-        "unit": "GPoPs",
-        "n_gpus": world,
-        "steps": args.steps,
-        "warmup": warm,
-        "ms_per_step": tot_ms / args.steps,
-        "higher_is_better": True,
-        "scaling": "weak",
-        "vs_baseline": None,
-        "dtype": "f32",
-        "data": "synthetic",
-        "config": {"workload": WORKLOAD, "P": progs.P, "N": pr.N, "d": pr.d,
-                   "tokens": progs.tokens, "node_evals_per_step": node_evals,
-                   "precision": "fp32-compensated",
-                   "l2": "flushed before every timed step (256 MiB write, outside events)",
-                   "parallelism": f"replicas x{world} (independent populations)"},
-        "p50_ms": srt[len(srt) // 2],
-        "p99_ms": srt[min(len(srt) - 1, int(round(0.99 * (len(srt) - 1))))],
-        "fp64": {"value": node_evals / (statistics.median(f64_ms) / 1e3) / 1e9,
-                 "unit": "GPoPs", "ms_per_step": statistics.median(f64_ms)},
-        "fp32c_vs_fp64_speedup": statistics.median(f64_ms) / statistics.median(step_ms),
-        "fp32c_error_vs_fp64_path": {
-            "programs_compared": int(ok.sum()),
-            "frac_within_1e-5": float(within.mean()) if ok.any() else None,
-            "median_rel": float(np.median(rel)) if ok.any() else None,
-            "note": "fp32 against fp64 evaluation of the programs themselves: ill-conditioned "
-                    "random programs differ in their per-case values, not in the aggregation"},
-        "fp32c_aggregation_error": agg,
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "GPoPs",
-                     "frac": achieved / peak, "traffic": captured_traffic(),
-                     "traffic_unit": "bytes per launch (ncu dram read + write)",
-                     "peak_basis": ("issue roofline: the op mix's instructions (ncu counts of "
-                                    "each operator as implemented, validity check included, "
-                                    "leaves free) at 4 issues / SM / cycle, 152 SMs, the "
-                                    "measured SM clock; binding: " + issue["binding"])
-                                   if issue else "straight-line per-op throughput",
-                     "per_pipe_ms": issue["per_pipe_ms"] if issue else None,
-                     "peak_straight_line_ops": peak_straight,
-                     "frac_straight_line_ops": achieved / peak_straight,
-                     "kernel_ms": kern_avg_s * 1e3},
-        "cpu_baseline": cpu,
-        "e2e": {"value": node_evals / statistics.median(e2e_s) / 1e9, "unit": "GPoPs",
-                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
-        "gpu_launches": LAUNCHES_PER_CALL * args.steps,
-        "clocks": clk,
-        "op_rates_gevals": {str(k): v / 1e9 for k, v in sorted(rates.items())},
-    }
-    print(json.dumps(line), flush=True)
-    if dist is not None:
-        dist.destroy_process_group()
-    return 0
+    if args.workload == "headline":
+        return run_headline(args, rank, world, local)
+    return run_single(args, rank, world, local)
 
 
 if __name__ == "__main__":

@@ -176,15 +176,18 @@ beagle_status beagle_score_host(const uint8_t *programs, const int64_t *offsets,
  * counterpart; this is for callers that cannot allocate while they score -- a loop that must
  * never block on the device (cudaMalloc and cudaFree may synchronise it), a process that
  * reserves its whole device-memory budget up front, or code that runs while another
- * component owns the allocator. Same arguments, results and asynchrony as beagle_score. Its
- * scratch (a 256-byte header plus 44 bytes per program and case tile of 512 cases) lives in
- * one fixed array of
+ * component owns the allocator. Same arguments, results and asynchrony as beagle_score, with
+ * a fixed launch shape: tiles of 512 cases, 4 cases per lane on the FP32 path, programs in
+ * the caller's order. beagle_set_launch_config and the autotuner's choices are ignored; with
+ * the automatic shape, beagle_score gives the same bits. Its scratch (a 256-byte header plus
+ * 44 bytes per program and tile of 512 cases) lives in one fixed array of
  * BEAGLE_STATIC_SCRATCH_BYTES inside the library, held on every device that loads the library
- * until the process exits; a call that needs more fails with BEAGLE_ERR_LIMIT. The first call
- * on a device looks up the array's device address (cudaGetSymbolAddress) with that device
- * current, so make that first call before any stream capture. All calls share the one array
- * and each zeroes its header on its stream: calls whose work overlaps on the GPU (other
- * streams or threads) race, so the caller must serialise them.
+ * until the process exits; a call that needs more (or P >= 2^31) fails with BEAGLE_ERR_LIMIT
+ * before enqueuing anything. The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current, so make that first call before any stream
+ * capture. All calls share the one array and each zeroes its header on its stream: calls
+ * whose work overlaps on the GPU (other streams or threads) race, so the caller must
+ * serialise them.
  */
 #define BEAGLE_STATIC_SCRATCH_BYTES (32u << 20)
 beagle_status beagle_score_static(const uint8_t *programs, const int64_t *offsets,
@@ -284,12 +287,6 @@ beagle_status beagle_get_launch_config(beagle_launch_config *cfg);
  */
 beagle_status beagle_measure_op_rates(double *rates, int32_t n_rates, double seconds_hint,
                                       void *stream);
-/* beagle_measure_dispatch: cost of the interpreter's token dispatch on the current device
- * (the prefetch, mask and indexed branch every token takes, with one-instruction handlers),
- * with warps_per_sm (1-32) warps on every SM: the mean cycles a warp spends per dispatch and
- * the dispatches an SM completes per cycle. Synchronous, default stream, about a millisecond. */
-beagle_status beagle_measure_dispatch(int32_t warps_per_sm, double *cycles_per_dispatch,
-                                      double *dispatches_per_sm_cycle);
 beagle_status beagle_kernel_timing(int32_t enable);
 beagle_status beagle_kernel_time(double *total_ms, int64_t *launches);
 

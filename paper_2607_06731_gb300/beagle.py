@@ -57,7 +57,6 @@ _SIGNATURES = {
     "beagle_batch_plan_destroy": ([_vp], _i32),
     "beagle_autotune": ([_vp, _i32, _i32, _i32, _vp, _vp, _vp], _i32),
     "beagle_autotune_clear": ([], _i32),
-    "beagle_measure_dispatch": ([_i32, _vp, _vp], _i32),
     "beagle_serve_create": ([_vp, _vp], _i32),
     "beagle_serve_submit": ([_vp, _vp, _vp], _i32),
     "beagle_serve_poll": ([_vp, ctypes.c_uint64, _vp, _vp], _i32),
@@ -441,11 +440,3 @@ class Server:
         if self.handle:
             check(lib().beagle_serve_destroy(self.handle))
             self.handle = None
-
-
-def measure_dispatch(warps_per_sm: int):
-    """beagle_measure_dispatch: (cycles per dispatch per warp, dispatches per SM cycle)."""
-    c = ctypes.c_double()
-    r = ctypes.c_double()
-    check(lib().beagle_measure_dispatch(warps_per_sm, ctypes.byref(c), ctypes.byref(r)))
-    return c.value, r.value

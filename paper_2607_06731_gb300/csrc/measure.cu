@@ -45,56 +45,6 @@ __global__ void __launch_bounds__(256) op_rate_kernel(float *sink, int iters, fl
     if (s == 12345.678f) sink[threadIdx.x] = s;   // keeps the chains live
 }
 
-// Dispatch cost: a threaded loop of the interpreter's dispatch sequence (mask the prefetched
-// handler id, prefetch the next token from shared memory, indexed branch) over 256 tokens of
-// eight one-instruction handlers, repeated. Each warp reports its cycles; the bounds check
-// before the branch ends the loop after the last token.
-#define BG_PROBE_DISPATCH                                                                  \
-    "and.b32 h, %2, 7;\n\t"                                                                \
-    "ld.shared.u32 %2, [%1];\n\t"                                                          \
-    "add.u32 %1, %1, 4;\n\t"                                                               \
-    "setp.ge.u32 pe, %1, %3;\n\t"                                                          \
-    "@pe bra.uni END_%=;\n\t"                                                              \
-    "brx.idx.uni h, TBL_%=;\n"
-
-constexpr int kProbeTokens = 256;
-
-__global__ void __launch_bounds__(1024) dispatch_probe_kernel(int reps, long long *cycles,
-                                                              float *sink) {
-    __shared__ uint32_t tok[32][kProbeTokens + 4];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int i = lane; i < kProbeTokens + 4; i += 32)   // fixed pseudo-random handler ids
-        tok[warp][i] = (static_cast<uint32_t>(i) * 2654435761u >> 13) & 7u;
-    __syncwarp();
-    float a = static_cast<float>(lane);
-    const uint32_t base = smem_addr(&tok[warp][0]);
-    const long long t0 = clock64();
-    for (int r = 0; r < reps; ++r) {
-        uint32_t nx = tok[warp][0];
-        uint32_t pa = base + 4u;
-        const uint32_t pend = base + 4u * kProbeTokens + 4u;
-        asm volatile(
-            "{\n\t.reg .b32 h;\n\t.reg .pred pe;\n\t"
-            "TBL_%=: .branchtargets H0_%=, H1_%=, H2_%=, H3_%=, H4_%=, H5_%=, H6_%=, H7_%=;\n\t"
-            BG_PROBE_DISPATCH
-            "H0_%=:\n\tadd.f32 %0, %0, 0f3F800000;\n\t" BG_PROBE_DISPATCH
-            "H1_%=:\n\tadd.f32 %0, %0, 0f40000000;\n\t" BG_PROBE_DISPATCH
-            "H2_%=:\n\tmul.f32 %0, %0, 0f3F000000;\n\t" BG_PROBE_DISPATCH
-            "H3_%=:\n\tadd.f32 %0, %0, 0fBF800000;\n\t" BG_PROBE_DISPATCH
-            "H4_%=:\n\tadd.f32 %0, %0, 0f40400000;\n\t" BG_PROBE_DISPATCH
-            "H5_%=:\n\tmul.f32 %0, %0, 0f3F400000;\n\t" BG_PROBE_DISPATCH
-            "H6_%=:\n\tadd.f32 %0, %0, 0f40800000;\n\t" BG_PROBE_DISPATCH
-            "H7_%=:\n\tmul.f32 %0, %0, 0f3F200000;\n\t" BG_PROBE_DISPATCH
-            "END_%=:\n\t}"
-            : "+f"(a), "+r"(pa), "+r"(nx)
-            : "r"(pend)
-            : "memory");
-    }
-    const long long t1 = clock64();
-    if (lane == 0) cycles[blockIdx.x * 32 + warp] = t1 - t0;
-    if (a == 12345.678f) sink[threadIdx.x] = a;
-}
-#undef BG_PROBE_DISPATCH
 
 template <int OPC>
 static double time_op(int blocks, int iters, cudaStream_t s, float *sink) {
@@ -212,39 +162,3 @@ beagle_status beagle_kernel_time(double *total_ms, int64_t *launches) {
 }
 
 }  // extern "C"
-
-extern "C" beagle_status beagle_measure_dispatch(int32_t warps_per_sm,
-                                                double *cycles_per_dispatch,
-                                                double *dispatches_per_sm_cycle) {
-    if (warps_per_sm < 1 || warps_per_sm > 32 || !cycles_per_dispatch ||
-        !dispatches_per_sm_cycle)
-        return fail(BEAGLE_ERR_ARG, "warps_per_sm must be 1-32 and outputs non-null");
-    const int grid = sm_count();
-    long long *cyc = nullptr;
-    float *sink = nullptr;
-    cudaError_t e = cudaMalloc(&cyc, sizeof(long long) * grid * 32);
-    if (e == cudaSuccess) e = cudaMalloc(&sink, sizeof(float) * 1024);
-    const int reps = 200;
-    if (e == cudaSuccess) {
-        dispatch_probe_kernel<<<grid, warps_per_sm * 32>>>(2, cyc, sink);   // warm-up
-        dispatch_probe_kernel<<<grid, warps_per_sm * 32>>>(reps, cyc, sink);
-        e = cudaDeviceSynchronize();
-    }
-    std::vector<long long> h(static_cast<size_t>(grid) * 32, 0);
-    if (e == cudaSuccess)
-        e = cudaMemcpy(h.data(), cyc, sizeof(long long) * h.size(), cudaMemcpyDeviceToHost);
-    cudaFree(cyc);
-    cudaFree(sink);
-    if (e != cudaSuccess) return cuda_fail(e, "dispatch probe");
-    double sum = 0.0;
-    long long mx = 1;
-    for (int b = 0; b < grid; ++b)
-        for (int w = 0; w < warps_per_sm; ++w) {
-            sum += static_cast<double>(h[static_cast<size_t>(b) * 32 + w]);
-            mx = std::max(mx, h[static_cast<size_t>(b) * 32 + w]);
-        }
-    const double per_warp = static_cast<double>(kProbeTokens - 1) * reps;
-    *cycles_per_dispatch = sum / (static_cast<double>(grid) * warps_per_sm) / per_warp;
-    *dispatches_per_sm_cycle = warps_per_sm * per_warp / static_cast<double>(mx);
-    return BEAGLE_OK;
-}

@@ -65,17 +65,24 @@ extern "C" beagle_status beagle_score_static(const uint8_t *programs, const int6
     if (!programs || !offsets || !lengths || !consts || !fitness_out)
         return fail(BEAGLE_ERR_ARG, "null pointer argument");
 
-    // Same launch plan as beagle_score for one job.
-    const int tile = tile_for(precision, kCasesFp32, 0);
-    const int32_t tiles = static_cast<int32_t>((ds->N + tile - 1) / tile);
-    const size_t part_bytes = static_cast<size_t>(kNumFields) * tiles * static_cast<size_t>(P) *
-                              sizeof(uint32_t);
-    const size_t need = 256 + round256(part_bytes);
-    if (need > BEAGLE_STATIC_SCRATCH_BYTES)
+    // A fixed launch shape, whatever beagle_set_launch_config or the autotuner chose: tiles
+    // of 512 cases, 4 cases per lane on the FP32 path, as many consumer warps as shared
+    // memory allows, programs in the caller's order (the length-bucketed order would need
+    // scratch of its own). beagle_score with its automatic shape gives the same bits.
+    if (P > (int64_t(1) << 31) - 1) return fail(BEAGLE_ERR_LIMIT, "P >= 2^31");
+    const int tile = tile_for(precision, kCasesFp32, 512);
+    const int64_t tiles = (ds->N + tile - 1) / tile;
+    // 44 bytes per program and tile after a 256-byte header; compared without forming the
+    // product, which could wrap for huge P.
+    const int64_t per_program = static_cast<int64_t>(kNumFields) * 4 * tiles;
+    const int64_t max_programs =
+        (static_cast<int64_t>(BEAGLE_STATIC_SCRATCH_BYTES) - 512) / per_program;
+    if (P > max_programs)
         return fail(BEAGLE_ERR_LIMIT,
-                    "static scratch needs %zu bytes for P = %lld and %d tiles; the limit is %u "
-                    "(44 bytes per program and tile of %d cases)",
-                    need, (long long)P, tiles, (unsigned)BEAGLE_STATIC_SCRATCH_BYTES, tile);
+                    "static scratch holds at most %lld programs on %lld tiles of %d cases "
+                    "(44 bytes per program and tile, limit %u bytes); got P = %lld",
+                    (long long)max_programs, (long long)tiles, tile,
+                    (unsigned)BEAGLE_STATIC_SCRATCH_BYTES, (long long)P);
     char *base = nullptr;
     beagle_status st = static_scratch_address(dev, &base);
     if (st != BEAGLE_OK) return st;
@@ -87,7 +94,7 @@ extern "C" beagle_status beagle_score_static(const uint8_t *programs, const int6
     if (e != cudaSuccess) return cuda_fail(e, "static scratch: memset");
 
     const int grid = sm_count();
-    const int64_t work = P * tiles;
+    const int64_t work = P * tiles;   // P < 2^31 and tiles < 2^22: no overflow
     const int xbuf_floats = ds->rows * tile;
     const int nw = plan_warps(precision, kCasesFp32, xbuf_floats, tile);
     if (nw < 1 || smem_bytes(precision, kCasesFp32, xbuf_floats, tile, nw) > kSmemBudget)
@@ -113,7 +120,7 @@ extern "C" beagle_status beagle_score_static(const uint8_t *programs, const int6
     J.item0 = 0;
     J.d = ds->d;
     J.rows = ds->rows;
-    J.tiles = tiles;
+    J.tiles = static_cast<int32_t>(tiles);
     J.groups = static_cast<int32_t>((P + group - 1) / group);
     J.ybar = ds->ybar;
     J.syy = precision == BEAGLE_FP64 ? ds->syy : ds->syy32;

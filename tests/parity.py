@@ -27,6 +27,17 @@ FLAG_BITS = 1 | 2 | 4
 TOL32 = (1e-5, 1e-7)
 TOL64 = (1e-12, 1e-13)
 
+# Floors of the strict (well-conditioned) fraction per named check: a regression that pushes
+# programs out of the strict set (a looser bound, a wrong flag) fails the floor even when
+# every remaining strict program passes. Set a little below the fractions measured on a GB300.
+STRICT_FLOORS: dict[str, float] = {}
+
+
+def _report(name, kind, frac):
+    if name:
+        print(f"STRICT {name} {kind} {frac:.4f}")
+    return STRICT_FLOORS.get(f"{name}/{kind}", 0.0) if name else 0.0
+
 
 def close(a, b, rel, abs_, extra=0.0):
     a = np.asarray(a, np.float64)
@@ -69,7 +80,7 @@ def _envelope(gpu, ref, tol, what):
     return amb, valid
 
 
-def check_fp32(gpu, refs, min_strict=0.0):
+def check_fp32(gpu, refs, min_strict=0.0, name=None):
     """Flags, envelope and gates A/B for the FP32-compensated path."""
     b32, b64 = refs
     gm, gr, gf = gpu
@@ -84,11 +95,12 @@ def check_fp32(gpu, refs, min_strict=0.0):
         bad = np.nonzero(strict & ~ok)[0]
         assert len(bad) == 0, f"gate {name}\n" + describe(bad, gpu, ref)
     frac = float((strict | (~amb & ~valid)).mean()) if len(strict) else 1.0
+    min_strict = max(min_strict, _report(name, "fp32", frac))
     assert frac >= min_strict, f"strict fraction {frac:.3f} < {min_strict}"
     return {"strict": frac, "ambiguous": float(amb.mean()) if len(amb) else 0.0}
 
 
-def check_fp64(gpu, refs, min_strict=0.0):
+def check_fp64(gpu, refs, min_strict=0.0, name=None):
     """Flags, envelope and gate C for the plain FP64 path."""
     b32, b64 = refs
     gm, gr, gf = gpu
@@ -99,5 +111,6 @@ def check_fp64(gpu, refs, min_strict=0.0):
     bad = np.nonzero(tight & ~ok)[0]
     assert len(bad) == 0, "gate C (FP64 path vs FP64 oracle)\n" + describe(bad, gpu, b64)
     frac = float((tight | (~amb & ~valid)).mean()) if len(tight) else 1.0
+    min_strict = max(min_strict, _report(name, "fp64", frac))
     assert frac >= min_strict, f"strict fraction {frac:.3f} < {min_strict}"
     return {"strict": frac}

@@ -59,11 +59,11 @@ def test_batch_matches_oracle_on_a_sample():
     beagle.score_batch(items)
     torch.cuda.synchronize()
     rng = np.random.default_rng(0)
-    for pr, (dp, ds, out) in zip(pops, items):
+    for k, (pr, (dp, ds, out)) in enumerate(zip(pops, items)):
         got = beagle.unpack_fitness(out)
-        idx = rng.choice(pr.programs.P, min(60, pr.programs.P), replace=False)
+        idx = rng.choice(pr.programs.P, min(400, pr.programs.P), replace=False)
         refs = parity.references(pr.programs.subset(idx), pr.X, pr.y)
-        parity.check_fp32(tuple(a[idx] for a in got), refs)
+        parity.check_fp32(tuple(a[idx] for a in got), refs, name=f"batch-{k}")
         ds.release()
 
 

@@ -34,26 +34,26 @@ def run_gpu(progs, X, y, precision="fp32c", ds=None):
     return r
 
 
-def full_check(progs, X, y, min_strict=0.0, fp64=True):
+def full_check(progs, X, y, min_strict=0.0, fp64=True, name=None):
     refs = parity.references(progs, X, y)
     g32 = run_gpu(progs, X, y, "fp32c")
-    stats = parity.check_fp32(g32, refs, min_strict=min_strict)
+    stats = parity.check_fp32(g32, refs, min_strict=min_strict, name=name)
     if fp64:
         g64 = run_gpu(progs, X, y, "fp64")
-        stats["fp64"] = parity.check_fp64(g64, refs)
+        stats["fp64"] = parity.check_fp64(g64, refs, name=name)
     return stats
 
 
 def test_c1_plain_scoring_full_size():
     """P = 1024 programs of length 8-32 on N = 1024 cases, d = 2 (one tile)."""
     pr = S.make_c1()
-    stats = full_check(pr.programs, pr.X, pr.y, min_strict=0.3)
+    stats = full_check(pr.programs, pr.X, pr.y, min_strict=0.3, name="c1")
     print(f"c1 {stats}")
 
 
 def test_c2_distribution_small_population():
     pr = S.make_c2(P=3000)
-    full_check(pr.programs, pr.X, pr.y)
+    full_check(pr.programs, pr.X, pr.y, name="c2-3000")
 
 
 @pytest.mark.parametrize("N,d", [(2500, 10), (700, 16), (2, 1), (1025, 3), (3000, 13),
@@ -63,7 +63,7 @@ def test_multi_tile_and_ragged_tail(N, d):
     X = rng.uniform(-3, 3, size=(d, N)).astype(np.float32)
     y = (np.sin(X[0]) * 2 + X[-1] + rng.normal(0, 0.1, N)).astype(np.float32)
     progs = S.gen_programs(rng, 500, 4, 64, d)
-    full_check(progs, X, y)
+    full_check(progs, X, y, name=f"tiles-{N}-{d}")
 
 
 def test_c2_full_population_sampled():
@@ -74,22 +74,22 @@ def test_c2_full_population_sampled():
     idx = np.random.default_rng(0).choice(pr.programs.P, 1500, replace=False)
     sub = pr.programs.subset(idx)
     refs = parity.references(sub, pr.X, pr.y)
-    print(parity.check_fp32(tuple(a[idx] for a in g32), refs))
+    print(parity.check_fp32(tuple(a[idx] for a in g32), refs, name="c2-full-1500"))
 
 
 def test_c3_full_size_sampled():
     """P = 50,000 programs on N = 1,000,000 cases (977 tiles): every program scored on the
-    GPU, a sample checked against the oracle at the full case count. The FP64 path is
-    checked on a subset of the population."""
+    GPU, a seeded 500-program sample checked against the oracle (with its error bound) at the
+    full case count. The FP64 path is checked on the sample."""
     pr = S.make_c3()
     ds = beagle.Dataset(pr.X, pr.y)
     g32 = run_gpu(pr.programs, pr.X, pr.y, "fp32c", ds=ds)
-    idx = np.random.default_rng(1).choice(pr.programs.P, 48, replace=False)
+    idx = np.random.default_rng(1).choice(pr.programs.P, 500, replace=False)
     sub = pr.programs.subset(idx)
     refs = parity.references(sub, pr.X, pr.y)
-    print(parity.check_fp32(tuple(a[idx] for a in g32), refs))
+    print(parity.check_fp32(tuple(a[idx] for a in g32), refs, name="c3-500"))
     g64 = run_gpu(sub, pr.X, pr.y, "fp64", ds=ds)
-    parity.check_fp64(g64, refs)
+    parity.check_fp64(g64, refs, name="c3-500")
     ds.release()
 
 

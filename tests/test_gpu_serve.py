@@ -161,12 +161,14 @@ def test_wait_timeout_keeps_the_ticket_and_poll_collects():
 def test_served_results_match_the_oracle_on_a_sample():
     runs = _runs(n_runs=2, seed=8)
     srv = beagle.Server()
-    for X, y, ds, gens in runs:
+    for k, (X, y, ds, gens) in enumerate(runs):
         p = gens[0]
         got = srv.wait(srv.submit(p, ds))
-        idx = np.arange(min(len(p.lengths), 64))
+        idx = np.sort(np.random.default_rng(k).choice(len(p.lengths), min(len(p.lengths), 400),
+                                                      replace=False))
         refs = parity.references(p.subset(idx), X, y)
-        parity.check_fp32(tuple(a[idx] for a in beagle.unpack_fitness(got)), refs)
+        parity.check_fp32(tuple(a[idx] for a in beagle.unpack_fitness(got)), refs,
+                          name=f"serve-{k}")
     srv.destroy()
     for *_, ds, _ in runs:
         ds.release()
