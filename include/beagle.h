@@ -66,10 +66,29 @@ typedef int32_t beagle_status;
 #define BEAGLE_OP_DUP    11   /* push a copy of the top */
 #define BEAGLE_OP_SWAP   12   /* exchange the top two */
 #define BEAGLE_OP_DEL    13   /* pop the top */
+/* The rest of Table 3, unprotected: a value outside an operator's domain is NaN (invalid). */
+#define BEAGLE_OP_POW    14   /* second ^ top */
+#define BEAGLE_OP_SIGN   15   /* -top ("changes the sign") */
+#define BEAGLE_OP_CUBE   16   /* (top top) top, each product rounded */
+#define BEAGLE_OP_CBRT   17
+#define BEAGLE_OP_TAN    18
+#define BEAGLE_OP_ASIN   19   /* ARCSIN */
+#define BEAGLE_OP_ACOS   20   /* ARCCOS */
+#define BEAGLE_OP_ATAN   21   /* ARCTAN */
+#define BEAGLE_OP_TANH   22
 #define BEAGLE_OP_LOAD0  32   /* BEAGLE_OP_LOAD0 + k pushes input x_k (k zero-based) */
+/* Table 3's variables: COPY @k copies the top into variable k (the stack is unchanged);
+ * PASTE @k pushes it and empties the variable. Each COPY @k must be followed by exactly one
+ * PASTE @k before the next COPY @k, and every variable must be empty at the end. On the GPU a
+ * live variable k occupies a stack slot: the stack depth plus (highest live k + 1) must not
+ * exceed the stack limit. */
+#define BEAGLE_OP_COPY0  64   /* BEAGLE_OP_COPY0 + k, k < BEAGLE_MAX_REGS */
+#define BEAGLE_OP_PASTE0 80   /* BEAGLE_OP_PASTE0 + k */
+#define BEAGLE_MAX_REGS   8
 
 #define BEAGLE_MAX_VARS    16    /* inputs per dataset (d) */
-#define BEAGLE_MAX_DEPTH   16    /* values on the GPU stack (the paper's StackSize is 32) */
+#define BEAGLE_MAX_DEPTH   32    /* values on the stack: the paper's StackSize (the GCL
+                                    section); programs deeper than 16 run in a second pass */
 #define BEAGLE_MAX_LENGTH  256   /* tokens per program */
 
 /* ---- Result flags ---- */
@@ -110,6 +129,18 @@ beagle_status beagle_upload_dataset(const float *X, const float *y, int64_t N, i
                                     int32_t inputs_on_device, void *stream,
                                     int32_t *dataset_id);
 
+/*
+ * beagle_upload_dataset with flags. BEAGLE_DATASET_INVALID_TARGETS: y may hold invalid
+ * targets (NaN, +-inf, |y| > 1e30), as the paper allows ("Fitness Functions": invalid values in
+ * the dataset are matched, not removed); X must still be valid. Such a dataset is scored with
+ * beagle_score_fit only (beagle_score returns BEAGLE_ERR_DATASET); its stored mean and sum of
+ * squares are over the valid targets, and it may hold a constant or empty set of valid targets.
+ */
+#define BEAGLE_DATASET_INVALID_TARGETS 1u
+beagle_status beagle_upload_dataset_ex(const float *X, const float *y, int64_t N, int32_t d,
+                                       int32_t inputs_on_device, uint32_t flags, void *stream,
+                                       int32_t *dataset_id);
+
 /* Release a dataset. Work already enqueued that uses it completes first (the call
  * synchronises the device). BEAGLE_ERR_DATASET for an unknown id, BEAGLE_ERR_BUSY while a
  * serving run still holds it. */
@@ -120,15 +151,28 @@ beagle_status beagle_dataset_info(int32_t dataset_id, int64_t *N, int32_t *d, do
                                   double *syy);
 
 /*
- * Host-side structural check of a population in the wire format (Section 3.2): every token
- * finds its operands, the stack never holds more than max_depth values, variables exist,
- * exactly one value remains, and 1 <= length <= BEAGLE_MAX_LENGTH. All pointers are host
- * pointers. Returns BEAGLE_ERR_PROGRAM and the index of the first bad program in
- * *first_bad (if not NULL), else BEAGLE_OK and -1.
+ * Host-side structural check of a population in the wire format (the GCL section): every
+ * token finds its operands, the stack never holds more than max_depth values, inputs exist,
+ * COPY and PASTE pair up, exactly one value remains, and 1 <= length <= BEAGLE_MAX_LENGTH. All
+ * pointers are host pointers. Returns BEAGLE_ERR_PROGRAM and the index of the first bad
+ * program in *first_bad (if not NULL), else BEAGLE_OK and -1. (max_depth and the 64-bit index
+ * extend the SURVEY's signature: the GPU's limit and the paper's StackSize differ.)
  */
 beagle_status beagle_validate_programs(const uint8_t *programs, const int64_t *offsets,
                                        const int32_t *lengths, int64_t P, int32_t d,
                                        int32_t max_depth, int64_t *first_bad);
+
+/*
+ * beagle_validate_programs with an operator whitelist ("Subclassing MLSetup - optional
+ * overrides": GetAllowedOperations restricts the operators a run may use). allowed lists
+ * n_allowed opcodes (host array); BEAGLE_OP_LOAD0 admits every LOAD, BEAGLE_OP_COPY0 every
+ * COPY and PASTE. n_allowed = 0 admits every operator. A program using another operator fails
+ * the check like a malformed one.
+ */
+beagle_status beagle_validate_programs_ex(const uint8_t *programs, const int64_t *offsets,
+                                          const int32_t *lengths, int64_t P, int32_t d,
+                                          int32_t max_depth, const uint8_t *allowed,
+                                          int32_t n_allowed, int64_t *first_bad);
 
 /*
  * Score a population against a resident dataset (Section 2.4). All array pointers are
@@ -148,6 +192,70 @@ beagle_status beagle_score(const uint8_t *programs, const int64_t *offsets,
                            const int32_t *lengths, const float *consts, int64_t P,
                            int32_t dataset_id, beagle_fitness *fitness_out,
                            int32_t precision, void *stream);
+
+/*
+ * The paper's own fitness functions ("Fitness Functions" in the framework overview, Eqs. 1-2;
+ * the configuration section's fitness functions, Eqs. 3-5; "Creating Custom Fit Functions":
+ * the IFitFunc interface, selected here per call by kind). Each fitness case is judged on its
+ * own: a case whose evaluation produced an invalid value (non-finite or |v| > 1e30, the rule
+ * above applied per case) is an invalid output; a target that is non-finite or above 1e30 is an
+ * invalid target (datasets uploaded with BEAGLE_DATASET_INVALID_TARGETS may hold them).
+ *   BEAGLE_FIT_CORRELATION  CorrelationFitFunc: r of Eq. 1 over the pairs where output and
+ *        target are both valid, then Eq. 2: score = M r^4 (N - (c1 + c2)) - M (c1 - c2), c1 =
+ *        pairs with exactly one invalid member, c2 = pairs with both invalid. r := 0 when it is
+ *        undefined (no valid pair, or outputs or targets constant over the valid pairs; flag
+ *        DEGENERATE).
+ *   BEAGLE_FIT_STD, _STD_SQUARE, _STD_CUBE, _STD_HYPER  Eq. 5 per case, summed (integer):
+ *        q = min(|f|,|y|) / max(|f|,|y|); M when both are 0; round(M q^k - M/11) when f and y
+ *        have opposite signs; round(M q^k) otherwise; k = 1, 2, 3, 8 (reading: the variants'
+ *        power applies to the ratio, so the best case still earns M). Pairs with an invalid
+ *        member (FitFunctionIfInvalid, reading): +M when both are invalid, -M when one is.
+ *        round() is to nearest, ties to even, in the path's precision (fp32 on the
+ *        FP32-compensated path).
+ *   BEAGLE_FIT_VALIDATE  the interactive V command's test ("Interacting with Beagle During a
+ *        Run"): a case passes when output and target are valid and |f - y| <= 0.001 |y|
+ *        (decided in fp64); score = passing cases; flag PERFECT when all N pass.
+ * asr = score / (M N) (the average score ratio of the sample run output; score / N for
+ * VALIDATE). taxed_score = score - tax_per_token * length: the parsimony pressure of
+ * ScriptLengthTaxRateInternal; tax_per_token < 0 selects its default rate M N / 85 (a
+ * perfect program of length 85 is taxed to zero). A malformed program scores -inf.
+ */
+#define BEAGLE_FIT_MSE_R2        0   /* beagle_score's MSE and 1 - r^2 (not for beagle_score_fit) */
+#define BEAGLE_FIT_CORRELATION   1
+#define BEAGLE_FIT_STD           2
+#define BEAGLE_FIT_STD_SQUARE    3
+#define BEAGLE_FIT_STD_CUBE      4
+#define BEAGLE_FIT_STD_HYPER     5
+#define BEAGLE_FIT_VALIDATE      6
+#define BEAGLE_FLAG_PERFECT     16u  /* VALIDATE: every case passed */
+
+typedef struct beagle_fit_config {
+    int32_t kind;            /* BEAGLE_FIT_* (not MSE_R2) */
+    int32_t max_score;       /* M, 1 .. 2^22 (the paper's sample run: 10,000 per case) */
+    double tax_per_token;    /* length tax; < 0: M N / 85 */
+} beagle_fit_config;
+
+typedef struct beagle_fit_result {   /* 56 bytes */
+    double score;            /* Eq. 2 score, sum of Eq. 5 rewards, or passing cases */
+    double asr;              /* score / (M N) (VALIDATE: score / N) */
+    double r2;               /* CORRELATION: r^2 over the valid pairs; else 0 */
+    double taxed_score;      /* score - tax_per_token * length */
+    int64_t c1;              /* pairs with exactly one invalid member */
+    int64_t c2;              /* pairs with both members invalid */
+    uint32_t flags;          /* BEAGLE_FLAG_DEGENERATE / MALFORMED / TIMEOUT / PERFECT */
+    uint32_t reserved;
+} beagle_fit_result;
+
+/*
+ * Score a population with one of the paper's fitness functions. Arguments as for beagle_score
+ * (device pointers), plus cfg (host pointer) and fit_out, a device array of P
+ * beagle_fit_result. Works on any dataset, including ones uploaded with
+ * BEAGLE_DATASET_INVALID_TARGETS. Asynchronous on stream.
+ */
+beagle_status beagle_score_fit(const uint8_t *programs, const int64_t *offsets,
+                               const int32_t *lengths, const float *consts, int64_t P,
+                               int32_t dataset_id, const beagle_fit_config *cfg,
+                               beagle_fit_result *fit_out, int32_t precision, void *stream);
 
 /*
  * Run each program on every case and keep the outputs (the paper's ExecuteGenome utility,
@@ -196,29 +304,41 @@ beagle_status beagle_score_static(const uint8_t *programs, const int64_t *offset
                                   int32_t precision, void *stream);
 
 /*
- * Serving (continuous batching). Many concurrent evolutionary runs each submit one generation
- * at a time -- a population in the wire format in HOST memory, scored against the run's
- * resident dataset (Section 2.4: genomes go to the device once per generation, one fitness per
- * genome comes back). The server copies each request into pinned staging recycled from a
- * pool (Section 2.7's dead pool), admits queued requests in arrival order while their device
- * bytes (inputs, outputs and scoring scratch) fit hbm_budget_bytes and a stream is free, packs
- * every admitted request into one persistent launch (one job each), and lets requests that
- * arrive meanwhile form the next launch on another stream. A request's results are the same
- * bits alone and in any mix. Datasets are held resident while a request uses them.
+ * Serving (continuous batching on the device). Many concurrent evolutionary runs each submit one
+ * generation at a time -- a population in the wire format in HOST memory, scored against the
+ * run's resident dataset ("Dividing Tasks Between CPU and GPU": genomes go to the device once
+ * per generation, one fitness per genome comes back). The server copies each request into
+ * pinned staging recycled from a pool (the dead pool of "CPU Optimizations"), admits queued
+ * requests in arrival order while their device bytes (inputs and scoring scratch) fit
+ * hbm_budget_bytes ("Hardware Optimized": batches fit device memory), and appends each as a
+ * job to the work queue of ONE persistent kernel that keeps running while requests arrive:
+ * a request admitted while others are on the GPU is scored between their work items, so a
+ * small request does not wait for a large one, and the kernel writes every program's fitness
+ * straight into the request's pinned output as soon as the program's last tile is done. The
+ * kernel exits when the server has no work and is launched again when work arrives. A
+ * request's results are the same bits alone, in any mix, and through beagle_score (tiles of
+ * 512 cases). Datasets are held resident while a request uses them; datasets with invalid
+ * targets are refused (BEAGLE_ERR_DATASET).
  *   submit   non-blocking; returns a ticket. A request larger than the budget fails with
  *            BEAGLE_ERR_OOM when it reaches the head of the queue.
  *   poll     *done = 1 and the results copied to host_out (P records) once finished; the
  *            ticket is then retired.
  *   wait     blocks until finished (timeout_us < 0: no limit); BEAGLE_ERR_TIMEOUT if not done
  *            in time (the ticket stays valid); on success retires the ticket.
+ *   timing   for a finished request (retired or not; the last 65,536 are kept): time queued
+ *            before admission and submit-to-result latency (microseconds, host clock), and
+ *            the device's %globaltimer stamps (ns) when its first work item was claimed and
+ *            when its last unit finished.
  *   stats    counters, node evaluations per second between the first submission and the last
- *            completion, and p50 / p99 / max latency (submit to result) of completed requests.
+ *            completion, and p50 / p99 / max latency (submit to result) of completed requests;
+ *            inflight_launches counts admitted requests not yet finished and launches the
+ *            persistent kernel's launches.
  *   destroy  finishes every queued and running request, then frees the server.
  */
 typedef struct beagle_serve_config {
     int64_t hbm_budget_bytes;   /* 0: half of the free device memory at creation */
-    int32_t max_inflight;       /* launches in flight at once (streams), 1-8; 0: 2 */
-    int32_t max_batch_jobs;     /* requests packed into one launch; 0: 64 */
+    int32_t max_inflight;       /* unused (0-8 accepted): the queue feeds one running kernel */
+    int32_t max_batch_jobs;     /* requests admitted per round of the serving thread; 0: 64 */
     int32_t precision;          /* BEAGLE_FP32_COMPENSATED or BEAGLE_FP64 */
     int32_t reserved;
 } beagle_serve_config;
@@ -248,6 +368,9 @@ beagle_status beagle_serve_poll(beagle_server *server, uint64_t ticket,
                                 beagle_fitness *host_out, int32_t *done);
 beagle_status beagle_serve_wait(beagle_server *server, uint64_t ticket,
                                 beagle_fitness *host_out, int64_t timeout_us);
+beagle_status beagle_serve_timing(beagle_server *server, uint64_t ticket, double *queue_us,
+                                  double *latency_us, uint64_t *gpu_start_ns,
+                                  uint64_t *gpu_end_ns);
 beagle_status beagle_serve_stats(beagle_server *server, beagle_serve_counters *stats);
 beagle_status beagle_serve_destroy(beagle_server *server);
 
@@ -340,6 +463,38 @@ beagle_status beagle_autotune(const beagle_job *jobs, int32_t n_jobs, int32_t pr
                               int32_t max_trials, void *stream, beagle_launch_config *best,
                               double *best_ms);
 beagle_status beagle_autotune_clear(void);
+
+/*
+ * Monte-Carlo ranking ("Monte-Carlo Ranking" in the overview; Table 2): the host side of a
+ * generation ranks the population without sorting it. A sample of 100 individuals (indices in
+ * sample, device [100], drawn by the caller) estimates the percentiles: its keys sorted
+ * ascending give thresholds t_q = the q-th order statistic, q = 10, 20, ..., 90. One pass then
+ * gives individual p its group g = the number of thresholds with key >= t_q (0-9; 9 is the
+ * ">= 90" row) and its children: floor(E_g) + (u[p] < E_g - floor(E_g)), E_g = Table 2's
+ * expected children (0.01, 0.03, 0.06, 0.15, 0.25, 0.5, 1, 1.5, 2.5, 4 for g = 0..9) and
+ * u[p] a uniform number in [0, 1) (device [P], drawn by the caller).
+ *   key               device pointer to the first record's key field, e.g. &fitness[0].mse
+ *                     or &fit_results[0].taxed_score; key_stride_bytes apart (24 / 56)
+ *   negate            1: lower values are better (MSE, 1 - r^2): the key is -value
+ * Higher keys are better; a NaN key ranks below every other (group 0), and a sample index
+ * outside [0, P) reads as NaN. Outputs: group_out [P] uint8, children_out [P] int32, device.
+ * n_sample must be 100. Asynchronous on stream.
+ */
+beagle_status beagle_rank(const double *key, int64_t key_stride_bytes, int32_t negate, int64_t P,
+                          const int64_t *sample, int32_t n_sample, const float *u,
+                          uint8_t *group_out, int32_t *children_out, void *stream);
+
+/*
+ * Population sharding by cost ("Hardware Optimized": the work of a generation is spread over
+ * every GPU of the machine): split programs [0, P) into n_shards contiguous ranges of nearly
+ * equal cost, a program's cost being its length (every program runs on the same cases).
+ * bounds_out[0..n_shards] (host) receives the range edges: shard k is [bounds[k],
+ * bounds[k+1]). Each shard's cost is within the longest program's length of total / n_shards.
+ * lengths is a host array. Each GPU then scores its shard with its own copy of the dataset; no
+ * collective is needed until the fitness records are gathered.
+ */
+beagle_status beagle_shard_by_cost(const int32_t *lengths, int64_t P, int32_t n_shards,
+                                   int64_t *bounds_out);
 
 /* Message of the calling thread's most recent failure ("" if none). */
 const char *beagle_last_error(void);

@@ -24,6 +24,10 @@ _LIB = os.path.join(_HERE, "liboracle.so")
 
 FP64, FP32 = 0, 1
 F_INVALID, F_DEGENERATE, F_MALFORMED, F_NEAR, F_AMBIG = 1, 2, 4, 256, 512
+F_PERFECT = 16
+# The paper's fitness functions (oracle_fit_score): correlation score of Eq. 2, the Eq. 5
+# point-to-point family, and the validation test of the interactive V command.
+FIT_CORRELATION, FIT_STD, FIT_STD_SQUARE, FIT_STD_CUBE, FIT_STD_HYPER, FIT_VALIDATE = range(1, 7)
 
 # The device's per-operator accuracy (units in the last place) used in the error bounds,
 # indexed by opcode. FP32 path: sin, cos, exp and the log within 2 ulp (CUDA documents 2 for
@@ -31,9 +35,14 @@ F_INVALID, F_DEGENERATE, F_MALFORMED, F_NEAR, F_AMBIG = 1, 2, 4, 256, 512
 # CUDA's documented bounds for double sin, cos, exp, log: 2, 2, 1, 1.
 DEV_ULPS_FP32 = {5: 2.0, 6: 2.0, 7: 2.0, 8: 2.0}
 DEV_ULPS_FP64 = {5: 2.0, 6: 2.0, 7: 1.0, 8: 1.0}
+# The rest of Table 3 (POW 14, CBRT 17, TAN 18, ARCSIN 19, ARCCOS 20, ARCTAN 21, TANH 22):
+# CUDA's powf, cbrtf, tanf, asinf, acosf, atanf, tanhf and their double versions, with the
+# bounds the GPU tests measure them against (tests/test_gpu_ops.py).
+DEV_ULPS_FP32.update({14: 8.0, 17: 2.0, 18: 4.0, 19: 4.0, 20: 4.0, 21: 4.0, 22: 4.0})
+DEV_ULPS_FP64.update({14: 2.0, 17: 2.0, 18: 2.0, 19: 2.0, 20: 2.0, 21: 2.0, 22: 2.0})
 STACK = 32
 CHECK_ERRORS = {0: "ok", 1: "underflow", 2: "overflow", 3: "final depth", 4: "opcode",
-                5: "variable", 6: "empty"}
+                5: "variable", 6: "empty", 7: "register"}
 
 _lib = None
 
@@ -72,6 +81,19 @@ def lib():
                                          ctypes.c_int32, ctypes.c_int32, P, ctypes.c_int32,
                                          P, P, P, P, P]
         L.oracle_score_bound.restype = ctypes.c_int
+        L.oracle_eval_cases.argtypes = [P, P, ctypes.c_int32, P, ctypes.c_int64,
+                                        ctypes.c_int32, ctypes.c_int32, P, P]
+        L.oracle_eval_cases.restype = ctypes.c_uint32
+        L.oracle_fit_aggregate.argtypes = [P, P, P, ctypes.c_int64, ctypes.c_uint32,
+                                           ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                           ctypes.c_double, ctypes.c_int32, P, P, P]
+        L.oracle_fit_aggregate.restype = None
+        L.oracle_fit_score.argtypes = [P, P, P, P, ctypes.c_int64, P, P, ctypes.c_int64,
+                                       ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                       ctypes.c_int32, ctypes.c_double, ctypes.c_int32, P, P, P]
+        L.oracle_fit_score.restype = ctypes.c_int
+        L.oracle_rank.argtypes = [P, ctypes.c_int64, P, ctypes.c_int32, P, P, P]
+        L.oracle_rank.restype = ctypes.c_int
         _lib = L
     return _lib
 
@@ -192,3 +214,72 @@ def score_bound(progs, X, y, mode="fp32", dev_ulps=None, nthreads: int = 0):
     if rc != 0:
         raise ValueError("oracle_score_bound rejected its arguments")
     return tuple(out)
+
+
+def eval_cases(ops, consts, X, mode="fp64"):
+    """Per-case outputs, per-case invalid markers (uint8) and flags of one program."""
+    ops = np.ascontiguousarray(ops, np.uint8)
+    consts = np.ascontiguousarray(consts, np.float32)
+    X = np.ascontiguousarray(X, np.float32)
+    if X.ndim == 1:
+        X = X[None, :]
+    d, N = X.shape
+    f = np.zeros(N, np.float64)
+    bad = np.zeros(N, np.uint8)
+    fl = lib().oracle_eval_cases(_p(ops), _p(consts), len(ops), _p(X), N, d, _mode(mode),
+                                 _p(f), _p(bad))
+    return f, bad, int(fl)
+
+
+def fit_aggregate(f, bad, y, kind, M=10_000, mode="fp64", tax=0.0, length=0, flags=0):
+    """(score, asr, r2, taxed, c1, c2, flags) from per-case outputs and invalid markers."""
+    f = np.ascontiguousarray(f, np.float64)
+    bad = np.ascontiguousarray(bad, np.uint8)
+    y = np.ascontiguousarray(y, np.float32)
+    out = np.zeros(4, np.float64)
+    cnt = np.zeros(2, np.int64)
+    fo = ctypes.c_uint32()
+    lib().oracle_fit_aggregate(_p(f), _p(bad), _p(y), len(y), flags, kind, M, _mode(mode),
+                               tax, length, _p(out), _p(cnt), ctypes.byref(fo))
+    return (*out.tolist(), int(cnt[0]), int(cnt[1]), fo.value)
+
+
+def fit_score(progs, X, y, kind, M=10_000, mode="fp64", tax=0.0, nthreads: int = 0):
+    """The paper's fitness of a population: (out [P][4] = score, asr, r2, taxed;
+    counts [P][2] = c1, c2; flags [P]). tax < 0 selects the default rate M N / 85."""
+    ops = np.ascontiguousarray(progs.ops, np.uint8)
+    offsets = np.ascontiguousarray(progs.offsets, np.int64)
+    lengths = np.ascontiguousarray(progs.lengths, np.int32)
+    consts = np.ascontiguousarray(progs.consts, np.float32)
+    X = np.ascontiguousarray(X, np.float32)
+    if X.ndim == 1:
+        X = X[None, :]
+    y = np.ascontiguousarray(y, np.float32)
+    d, N = X.shape
+    P = len(lengths)
+    out = np.zeros((P, 4), np.float64)
+    cnt = np.zeros((P, 2), np.int64)
+    flags = np.zeros(P, np.uint32)
+    rc = lib().oracle_fit_score(_p(ops), _p(offsets), _p(lengths), _p(consts), P, _p(X), _p(y),
+                                N, d, _mode(mode), kind, M, tax, nthreads, _p(out), _p(cnt),
+                                _p(flags))
+    if rc != 0:
+        raise ValueError("oracle_fit_score rejected its arguments")
+    return out, cnt, flags
+
+
+TABLE2_CHILDREN = (0.01, 0.03, 0.06, 0.15, 0.25, 0.5, 1.0, 1.5, 2.5, 4.0)
+
+
+def rank(key, sample, u):
+    """Monte-Carlo ranking: (group uint8 [P], children int32 [P]) from keys (higher is
+    better), the 100 sampled indices and one uniform number per individual."""
+    key = np.ascontiguousarray(key, np.float64)
+    sample = np.ascontiguousarray(sample, np.int64)
+    u = np.ascontiguousarray(u, np.float32)
+    P = len(key)
+    group = np.zeros(P, np.uint8)
+    children = np.zeros(P, np.int32)
+    if lib().oracle_rank(_p(key), P, _p(sample), len(sample), _p(u), _p(group), _p(children)):
+        raise ValueError("oracle_rank rejected its arguments")
+    return group, children

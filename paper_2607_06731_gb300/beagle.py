@@ -23,11 +23,27 @@ ERRORS = {-1: "BEAGLE_ERR_ARG", -2: "BEAGLE_ERR_PROGRAM", -3: "BEAGLE_ERR_DATASE
           -7: "BEAGLE_ERR_BUSY", -8: "BEAGLE_ERR_LIMIT"}
 FP32_COMPENSATED, FP64 = 0, 1
 FLAG_INVALID, FLAG_DEGENERATE, FLAG_MALFORMED, FLAG_TIMEOUT = 1, 2, 4, 8
-MAX_VARS, MAX_DEPTH, MAX_LENGTH = 16, 16, 256
+MAX_VARS, MAX_DEPTH, MAX_LENGTH = 16, 32, 256
 
 # beagle_fitness: {double mse; double one_minus_r2; uint32 flags; uint32 reserved}
 FITNESS_DTYPE = np.dtype([("mse", "<f8"), ("one_minus_r2", "<f8"), ("flags", "<u4"),
                           ("reserved", "<u4")])
+
+# The paper's fitness functions (beagle_score_fit)
+FIT_CORRELATION, FIT_STD, FIT_STD_SQUARE, FIT_STD_CUBE, FIT_STD_HYPER, FIT_VALIDATE = range(1, 7)
+FLAG_PERFECT = 16
+DATASET_INVALID_TARGETS = 1
+# beagle_fit_result: {double score, asr, r2, taxed_score; int64 c1, c2; uint32 flags, reserved}
+FIT_RESULT_DTYPE = np.dtype([("score", "<f8"), ("asr", "<f8"), ("r2", "<f8"),
+                             ("taxed_score", "<f8"), ("c1", "<i8"), ("c2", "<i8"),
+                             ("flags", "<u4"), ("reserved", "<u4")])
+
+
+class FitConfig(ctypes.Structure):
+    """beagle_fit_config."""
+    _fields_ = [("kind", ctypes.c_int32), ("max_score", ctypes.c_int32),
+                ("tax_per_token", ctypes.c_double)]
+
 
 HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
                       "include", "beagle.h")
@@ -44,9 +60,12 @@ _vp, _i32, _i64, _u8p = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.
 
 _SIGNATURES = {
     "beagle_upload_dataset": ([_vp, _vp, _i64, _i32, _i32, _vp, _vp], _i32),
+    "beagle_upload_dataset_ex": ([_vp, _vp, _i64, _i32, _i32, ctypes.c_uint32, _vp, _vp], _i32),
+    "beagle_score_fit": ([_vp, _vp, _vp, _vp, _i64, _i32, _vp, _vp, _i32, _vp], _i32),
     "beagle_release_dataset": ([_i32], _i32),
     "beagle_dataset_info": ([_i32, _vp, _vp, _vp, _vp], _i32),
     "beagle_validate_programs": ([_vp, _vp, _vp, _i64, _i32, _i32, _vp], _i32),
+    "beagle_validate_programs_ex": ([_vp, _vp, _vp, _i64, _i32, _i32, _vp, _i32, _vp], _i32),
     "beagle_score": ([_vp, _vp, _vp, _vp, _i64, _i32, _vp, _i32, _vp], _i32),
     "beagle_score_static": ([_vp, _vp, _vp, _vp, _i64, _i32, _vp, _i32, _vp], _i32),
     "beagle_eval": ([_vp, _vp, _vp, _vp, _i64, _i32, _vp, _vp, _i32, _vp], _i32),
@@ -62,6 +81,9 @@ _SIGNATURES = {
     "beagle_serve_poll": ([_vp, ctypes.c_uint64, _vp, _vp], _i32),
     "beagle_serve_wait": ([_vp, ctypes.c_uint64, _vp, _i64], _i32),
     "beagle_serve_stats": ([_vp, _vp], _i32),
+    "beagle_serve_timing": ([_vp, ctypes.c_uint64, _vp, _vp, _vp, _vp], _i32),
+    "beagle_rank": ([_vp, _i64, _i32, _i64, _vp, _i32, _vp, _vp, _vp, _vp], _i32),
+    "beagle_shard_by_cost": ([_vp, _i64, _i32, _vp], _i32),
     "beagle_serve_destroy": ([_vp], _i32),
     "beagle_set_launch_config": ([_vp], _i32),
     "beagle_get_launch_config": ([_vp], _i32),
@@ -134,7 +156,7 @@ def _ptr(t):
 class Dataset:
     """A dataset resident on the current device (beagle_upload_dataset)."""
 
-    def __init__(self, X, y, stream=None):
+    def __init__(self, X, y, stream=None, invalid_targets: bool = False):
         import torch
         on_device = isinstance(X, torch.Tensor) and X.is_cuda
         if on_device:
@@ -149,9 +171,10 @@ class Dataset:
         if int(y.shape[0]) != N:
             raise ValueError("y must have N entries")
         out = ctypes.c_int32()
-        check(lib().beagle_upload_dataset(_ptr(X), _ptr(y), N, d, int(on_device),
-                                          _stream_handle(stream) if on_device else None,
-                                          ctypes.byref(out)))
+        check(lib().beagle_upload_dataset_ex(_ptr(X), _ptr(y), N, d, int(on_device),
+                                             DATASET_INVALID_TARGETS if invalid_targets else 0,
+                                             _stream_handle(stream) if on_device else None,
+                                             ctypes.byref(out)))
         self.id = int(out.value)
         self.N, self.d = N, d
         yb, syy = ctypes.c_double(), ctypes.c_double()
@@ -173,14 +196,19 @@ def release_dataset(ds: Dataset):
 
 
 # ----------------------------------------------------------------------------- programs
-def validate_programs(ops, offsets, lengths, d: int, max_depth: int = MAX_DEPTH):
-    """Host structural check; returns -1 if all programs are valid, else the first bad index."""
+def validate_programs(ops, offsets, lengths, d: int, max_depth: int = MAX_DEPTH,
+                      allowed=None):
+    """Host structural check (beagle_validate_programs_ex): -1 if all programs are valid,
+    else the first bad index. allowed: optional opcode whitelist."""
     ops = np.ascontiguousarray(ops, np.uint8)
     offsets = np.ascontiguousarray(offsets, np.int64)
     lengths = np.ascontiguousarray(lengths, np.int32)
     first = ctypes.c_int64(-1)
-    rc = lib().beagle_validate_programs(_ptr(ops), _ptr(offsets), _ptr(lengths), len(lengths),
-                                        d, max_depth, ctypes.byref(first))
+    al = np.ascontiguousarray(allowed if allowed is not None else [], np.uint8)
+    rc = lib().beagle_validate_programs_ex(_ptr(ops), _ptr(offsets), _ptr(lengths),
+                                           len(lengths), d, max_depth,
+                                           _ptr(al) if len(al) else None, len(al),
+                                           ctypes.byref(first))
     if rc not in (OK, -2):
         check(rc)
     return int(first.value)
@@ -219,6 +247,26 @@ def score(programs, offsets, lengths, consts, dataset: Dataset, out=None,
                              dataset.id, _ptr(out), _precision(precision),
                              _stream_handle(stream)))
     return out
+
+
+def score_fit(dp: "DevicePrograms", dataset: "Dataset", kind: int, max_score: int = 10_000,
+              tax_per_token: float = 0.0, precision="fp32c", out=None, stream=None):
+    """beagle_score_fit: the paper's fitness functions. Returns (and fills) a [P, 7] float64
+    CUDA tensor whose rows are the 56-byte beagle_fit_result records (see unpack_fit)."""
+    import torch
+    if out is None:
+        out = torch.empty((dp.P, 7), dtype=torch.float64, device=dp.lengths.device)
+    cfg = FitConfig(kind, max_score, tax_per_token)
+    check(lib().beagle_score_fit(_ptr(dp.ops), _ptr(dp.offsets), _ptr(dp.lengths),
+                                 _ptr(dp.consts), dp.P, dataset.id, ctypes.byref(cfg), _ptr(out),
+                                 _precision(precision), _stream_handle(stream)))
+    return out
+
+
+def unpack_fit(out):
+    """Structured numpy array (FIT_RESULT_DTYPE) from a [P, 7] tensor."""
+    a = out.detach().cpu().numpy()
+    return np.ascontiguousarray(a).view(FIT_RESULT_DTYPE).reshape(-1).copy()
 
 
 def eval_programs(dp: "DevicePrograms", dataset: "Dataset", precision="fp32c", stream=None):
@@ -431,6 +479,16 @@ class Server:
         check(rc)
         return out
 
+    def timing(self, ticket: int) -> dict:
+        """Queue time and latency (us, host clock) and the device's %globaltimer stamps (ns) of
+        a finished request (beagle_serve_timing)."""
+        q, lat = ctypes.c_double(), ctypes.c_double()
+        g0, g1 = ctypes.c_uint64(), ctypes.c_uint64()
+        check(lib().beagle_serve_timing(self.handle, ticket, ctypes.byref(q), ctypes.byref(lat),
+                                        ctypes.byref(g0), ctypes.byref(g1)))
+        return {"queue_us": q.value, "latency_us": lat.value, "gpu_start_ns": g0.value,
+                "gpu_end_ns": g1.value}
+
     def stats(self) -> dict:
         st = ServeStats()
         check(lib().beagle_serve_stats(self.handle, ctypes.byref(st)))
@@ -440,3 +498,34 @@ class Server:
         if self.handle:
             check(lib().beagle_serve_destroy(self.handle))
             self.handle = None
+
+
+# ----------------------------------------------------------------------------- a generation
+def rank(fitness, sample, u, field: str = "mse", stream=None):
+    """beagle_rank (Monte-Carlo ranking) over fitness records on the device: a [P, 3] tensor
+    of beagle_fitness (field "mse" or "one_minus_r2": lower is better) or a [P, 7] tensor of
+    beagle_fit_result (field "score", "asr" or "taxed_score": higher is better). sample: 100
+    device int64 indices; u: [P] device float32 uniforms. Returns (group uint8, children int32)
+    device tensors."""
+    import torch
+    P = int(fitness.shape[0])
+    if fitness.shape[1] == 3:
+        off = {"mse": 0, "one_minus_r2": 8}[field]
+        stride, neg = 24, 1
+    else:
+        off = {"score": 0, "asr": 8, "taxed_score": 24}[field]
+        stride, neg = 56, 0
+    group = torch.empty(P, dtype=torch.uint8, device=fitness.device)
+    children = torch.empty(P, dtype=torch.int32, device=fitness.device)
+    check(lib().beagle_rank(_ptr(fitness) + off, stride, neg, P, _ptr(sample), int(sample.numel()),
+                            _ptr(u), _ptr(group), _ptr(children), _stream_handle(stream)))
+    return group, children
+
+
+def shard_by_cost(lengths, n_shards: int):
+    """beagle_shard_by_cost: [n_shards + 1] int64 range edges of programs split by summed
+    length."""
+    lengths = np.ascontiguousarray(lengths, np.int32)
+    bounds = np.zeros(n_shards + 1, np.int64)
+    check(lib().beagle_shard_by_cost(_ptr(lengths), len(lengths), n_shards, _ptr(bounds)))
+    return bounds

@@ -4,6 +4,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <limits>
 #include <memory>
 #include <mutex>
 #include <string>
@@ -110,7 +111,15 @@ int32_t beagle_version(void) { return 100; }
 beagle_status beagle_upload_dataset(const float *X, const float *y, int64_t N, int32_t d,
                                     int32_t inputs_on_device, void *stream,
                                     int32_t *dataset_id) {
+    return beagle_upload_dataset_ex(X, y, N, d, inputs_on_device, 0u, stream, dataset_id);
+}
+
+beagle_status beagle_upload_dataset_ex(const float *X, const float *y, int64_t N, int32_t d,
+                                       int32_t inputs_on_device, uint32_t flags, void *stream,
+                                       int32_t *dataset_id) {
     if (!X || !y || !dataset_id) return fail(BEAGLE_ERR_ARG, "null pointer argument");
+    if (flags & ~BEAGLE_DATASET_INVALID_TARGETS) return fail(BEAGLE_ERR_ARG, "unknown flags");
+    const bool allow_invalid = (flags & BEAGLE_DATASET_INVALID_TARGETS) != 0;
     if (N < 2) return fail(BEAGLE_ERR_ARG, "N must be >= 2 (got %lld)", (long long)N);
     if (d < 1 || d > BEAGLE_MAX_VARS)
         return fail(BEAGLE_ERR_LIMIT, "d must be in [1, %d] (got %d)", BEAGLE_MAX_VARS, d);
@@ -130,19 +139,28 @@ beagle_status beagle_upload_dataset(const float *X, const float *y, int64_t N, i
     for (size_t i = 0; i < hx.size(); ++i)
         if (!(std::fabs(static_cast<double>(hx[i])) <= 1e30))
             return fail(BEAGLE_ERR_DATASET, "X value %zu is non-finite or above 1e30", i);
+    // Mean and sum of squares of the valid targets (all of them, unless invalid targets are
+    // allowed).
+    auto valid_y = [](float v) { return std::fabs(static_cast<double>(v)) <= 1e30; };
     Acc sy;
+    int64_t nvalid = 0;
     for (int64_t i = 0; i < N; ++i) {
-        if (!(std::fabs(static_cast<double>(hy[i])) <= 1e30))
+        if (!valid_y(hy[i])) {
+            if (allow_invalid) continue;
             return fail(BEAGLE_ERR_DATASET, "y value %lld is non-finite or above 1e30", (long long)i);
+        }
         sy.add(hy[i]);
+        ++nvalid;
     }
-    const double ybar = sy.value() / static_cast<double>(N);
+    const double ybar = nvalid ? sy.value() / static_cast<double>(nvalid) : 0.0;
     Acc syy;
     for (int64_t i = 0; i < N; ++i) {
+        if (!valid_y(hy[i])) continue;
         const double c = static_cast<double>(hy[i]) - ybar;
         syy.add(c * c);
     }
-    if (!(syy.value() > 0.0)) return fail(BEAGLE_ERR_DATASET, "y is constant (S_yy = 0)");
+    if (!allow_invalid && !(syy.value() > 0.0))
+        return fail(BEAGLE_ERR_DATASET, "y is constant (S_yy = 0)");
 
     auto ds = std::make_shared<Dataset>();
     ds->N = N;
@@ -151,6 +169,7 @@ beagle_status beagle_upload_dataset(const float *X, const float *y, int64_t N, i
     ds->npad = (N + 63) / 64 * 64;
     ds->ybar = ybar;
     ds->syy = syy.value();
+    ds->invalid_targets = allow_invalid;
     cudaGetDevice(&ds->device);
     const int64_t npad = ds->npad;
     std::vector<float> lay(static_cast<size_t>(ds->rows) * npad, 0.0f);
@@ -160,6 +179,10 @@ beagle_status beagle_upload_dataset(const float *X, const float *y, int64_t N, i
     float *yc = &lay[static_cast<size_t>(d + 1) * npad];
     Acc syy32;
     for (int64_t i = 0; i < N; ++i) {
+        if (!valid_y(hy[i])) {   // an invalid target: the centred row holds NaN there
+            yc[i] = std::numeric_limits<float>::quiet_NaN();
+            continue;
+        }
         yc[i] = static_cast<float>(static_cast<double>(hy[i]) - ybar);
         syy32.add(static_cast<double>(yc[i]) * static_cast<double>(yc[i]));
     }
@@ -174,6 +197,7 @@ beagle_status beagle_upload_dataset(const float *X, const float *y, int64_t N, i
         for (int64_t t = 0; t < T; ++t) {
             Acc a, a64;
             for (int64_t i = t * tile; i < std::min(N, (t + 1) * tile); ++i) {
+                if (!valid_y(hy[i])) continue;
                 a.add(yc[i]);
                 a64.add(static_cast<double>(hy[i]) - ybar);
             }
@@ -245,14 +269,35 @@ beagle_status beagle_dataset_info(int32_t dataset_id, int64_t *N, int32_t *d, do
 beagle_status beagle_validate_programs(const uint8_t *programs, const int64_t *offsets,
                                        const int32_t *lengths, int64_t P, int32_t d,
                                        int32_t max_depth, int64_t *first_bad) {
+    return beagle_validate_programs_ex(programs, offsets, lengths, P, d, max_depth, nullptr, 0,
+                                       first_bad);
+}
+
+beagle_status beagle_validate_programs_ex(const uint8_t *programs, const int64_t *offsets,
+                                          const int32_t *lengths, int64_t P, int32_t d,
+                                          int32_t max_depth, const uint8_t *allowed,
+                                          int32_t n_allowed, int64_t *first_bad) {
     if (first_bad) *first_bad = -1;
     if (P < 0 || (P > 0 && (!programs || !offsets || !lengths)))
         return fail(BEAGLE_ERR_ARG, "bad arguments");
+    if (n_allowed < 0 || (n_allowed > 0 && !allowed)) return fail(BEAGLE_ERR_ARG, "bad allowed list");
+    // operator kind of a token for the whitelist: LOAD_k -> LOAD0, COPY/PASTE_k -> COPY0
+    auto kind_of = [](int op) {
+        if (op >= BEAGLE_OP_LOAD0 && op < BEAGLE_OP_LOAD0 + BEAGLE_MAX_VARS) return BEAGLE_OP_LOAD0;
+        if ((op >= BEAGLE_OP_COPY0 && op < BEAGLE_OP_COPY0 + BEAGLE_MAX_REGS) ||
+            (op >= BEAGLE_OP_PASTE0 && op < BEAGLE_OP_PASTE0 + BEAGLE_MAX_REGS))
+            return BEAGLE_OP_COPY0;
+        return op;
+    };
+    bool ok_kind[256];
+    for (int k = 0; k < 256; ++k) ok_kind[k] = n_allowed == 0;
+    for (int32_t i = 0; i < n_allowed; ++i) ok_kind[kind_of(allowed[i])] = true;
     for (int64_t p = 0; p < P; ++p) {
         const int32_t L = lengths[p];
         const char *why = nullptr;
         if (L < 1 || L > BEAGLE_MAX_LENGTH) why = "length out of [1, BEAGLE_MAX_LENGTH]";
         int depth = 0;
+        bool full[BEAGLE_MAX_REGS] = {false};
         for (int32_t j = 0; !why && j < L; ++j) {
             const int op = programs[offsets[p] + j];
             int need = 0, delta = 0;
@@ -260,16 +305,30 @@ beagle_status beagle_validate_programs(const uint8_t *programs, const int64_t *o
             else if (op >= BEAGLE_OP_LOAD0 && op < BEAGLE_OP_LOAD0 + BEAGLE_MAX_VARS) {
                 if (op - BEAGLE_OP_LOAD0 >= d) why = "variable index >= d";
                 delta = 1;
-            } else if (op >= BEAGLE_OP_ADD && op <= BEAGLE_OP_PDIV) { need = 2; delta = -1; }
-            else if (op >= BEAGLE_OP_SIN && op <= BEAGLE_OP_SQUARE) need = 1;
-            else if (op == BEAGLE_OP_DUP) { need = 1; delta = 1; }
+            } else if ((op >= BEAGLE_OP_ADD && op <= BEAGLE_OP_PDIV) || op == BEAGLE_OP_POW) {
+                need = 2; delta = -1;
+            } else if ((op >= BEAGLE_OP_SIN && op <= BEAGLE_OP_SQUARE) ||
+                       (op >= BEAGLE_OP_SIGN && op <= BEAGLE_OP_TANH)) {
+                need = 1;
+            } else if (op == BEAGLE_OP_DUP) { need = 1; delta = 1; }
             else if (op == BEAGLE_OP_SWAP) need = 2;
             else if (op == BEAGLE_OP_DEL) { need = 1; delta = -1; }
-            else why = "unknown opcode";
+            else if (op >= BEAGLE_OP_COPY0 && op < BEAGLE_OP_COPY0 + BEAGLE_MAX_REGS) {
+                need = 1;
+                if (full[op - BEAGLE_OP_COPY0]) why = "COPY into a variable that is still full";
+                full[op - BEAGLE_OP_COPY0] = true;
+            } else if (op >= BEAGLE_OP_PASTE0 && op < BEAGLE_OP_PASTE0 + BEAGLE_MAX_REGS) {
+                delta = 1;
+                if (!full[op - BEAGLE_OP_PASTE0]) why = "PASTE of an empty variable";
+                full[op - BEAGLE_OP_PASTE0] = false;
+            } else why = "unknown opcode";
+            if (!why && !ok_kind[kind_of(op)]) why = "operator not in the allowed list";
             if (!why && depth < need) why = "stack underflow";
             depth += delta;
             if (!why && depth > max_depth) why = "stack deeper than max_depth";
         }
+        for (int k = 0; !why && k < BEAGLE_MAX_REGS; ++k)
+            if (full[k]) why = "COPY without a PASTE";
         if (!why && depth != 1) why = "program does not leave exactly one value";
         if (why) {
             if (first_bad) *first_bad = p;
@@ -285,6 +344,28 @@ beagle_status beagle_score(const uint8_t *programs, const int64_t *offsets,
                            int32_t precision, void *stream) {
     JobRequest req{programs, offsets, lengths, consts, P, dataset_id, fitness_out, nullptr,
                    nullptr};
+    return score_jobs(&req, 1, precision, static_cast<cudaStream_t>(stream), nullptr);
+}
+
+beagle_status beagle_score_fit(const uint8_t *programs, const int64_t *offsets,
+                               const int32_t *lengths, const float *consts, int64_t P,
+                               int32_t dataset_id, const beagle_fit_config *cfg,
+                               beagle_fit_result *fit_out, int32_t precision, void *stream) {
+    if (!cfg) return fail(BEAGLE_ERR_ARG, "null fitness configuration");
+    if (cfg->kind < BEAGLE_FIT_CORRELATION || cfg->kind > BEAGLE_FIT_VALIDATE)
+        return fail(BEAGLE_ERR_ARG, "unknown fitness kind %d", cfg->kind);
+    if (cfg->max_score < 1 || cfg->max_score > (1 << 22))
+        return fail(BEAGLE_ERR_ARG, "max_score must be in [1, 2^22] (got %d)", cfg->max_score);
+    auto ds = find_dataset(dataset_id);
+    if (!ds) return fail(BEAGLE_ERR_DATASET, "unknown dataset %d", dataset_id);
+    JobRequest req{programs, offsets, lengths, consts, P, dataset_id, nullptr, nullptr,
+                   nullptr};
+    req.kind = cfg->kind;
+    req.max_score = cfg->max_score;
+    req.tax = cfg->tax_per_token >= 0.0
+                  ? cfg->tax_per_token
+                  : static_cast<double>(cfg->max_score) * static_cast<double>(ds->N) / 85.0;
+    req.fit = fit_out;
     return score_jobs(&req, 1, precision, static_cast<cudaStream_t>(stream), nullptr);
 }
 

@@ -11,7 +11,10 @@ namespace beagle {
 
 constexpr int kBox = 256;                         // cases per TMA box (box dims <= 256)
 constexpr int kMaxRows = BEAGLE_MAX_VARS + 2;     // x_0..x_{d-1}, y, y - mean(y)
-constexpr int kMaxDepth = BEAGLE_MAX_DEPTH;
+constexpr int kMaxDepth = BEAGLE_MAX_DEPTH;        // the paper's StackSize (32)
+constexpr int kDepthFast = 16;                     // stack of the default scoring pass
+// Scratch header of a launch: work counter, error word, one deep-program count per job.
+constexpr size_t kHdrCounter = 0, kHdrError = 128, kHdrDeep = 256, kHdrBytes = 512;
 constexpr int kMaxLen = BEAGLE_MAX_LENGTH;
 constexpr int kMaxJobs = 64;                      // (population, dataset) pairs per launch
 
@@ -28,6 +31,36 @@ enum Field : int {
     kMean64 = 10,   // FP64 path: second word of the fp64 centring value
     kNumFields = 11
 };
+
+// Per-(program, tile) partial sums of the paper's fitness functions (beagle_score_fit), same
+// field-major layout. Correlation: the centred sums over the tile's valid pairs (both output
+// and target valid), their count, c1 / c2 counts and the extremes of the valid outputs and
+// targets (constancy is decided exactly from them); pairs are compensated fp32 pairs on the
+// FP32 path, fp64 values on the FP64 path, scaled by 2^-kd (outputs) and 2^-ky (targets).
+// Eq. 5 family and validation: the tile's integer score (two words) and c1 / c2.
+enum FitField : int {
+    kfMean = 0,      // centring value of the valid outputs (T: 1 or 2 words)
+    kfN = 2,         // valid pairs
+    kfC1 = 3,        // pairs with exactly one invalid member
+    kfC2 = 4,        // pairs with both invalid
+    kfSd = 5,        // sum (f - m) 2^-kd            (2 words)
+    kfSdd = 7,       // sum ((f - m) 2^-kd)^2        (2 words)
+    kfSdy = 9,       // sum (f - m) 2^-kd yc 2^-ky   (2 words)
+    kfSy = 11,       // sum yc 2^-ky                 (2 words)
+    kfSyy = 13,      // sum (yc 2^-ky)^2             (2 words)
+    kfFmin = 15,     // smallest and largest valid output (T: 1 or 2 words each)
+    kfFmax = 17,
+    kfYmin = 19,     // smallest and largest valid target (fp32)
+    kfYmax = 20,
+    kfFlags = 21,    // TF_* bits | kd << 16 | ky << 24
+    kNumFitFields = 22,
+    kfScore = 5,     // Eq. 5 family / validation: int64 score of the tile (2 words)
+};
+
+// Fitness kinds of a job (include/beagle.h BEAGLE_FIT_*).
+constexpr int kFitMse = BEAGLE_FIT_MSE_R2, kFitCorr = BEAGLE_FIT_CORRELATION,
+              kFitStd = BEAGLE_FIT_STD, kFitStdHyper = BEAGLE_FIT_STD_HYPER,
+              kFitValidate = BEAGLE_FIT_VALIDATE;
 
 enum TileFlag : uint32_t {
     TF_INVALID = 1u,     // some case produced a non-finite value or |v| > 1e30
@@ -51,6 +84,12 @@ struct JobDev {
     int64_t item0;           // first global work item of this job
     int32_t d, rows, tiles, groups;
     double ybar, syy;
+    int32_t *deep_list;      // [P] programs deeper than the fast pass's stack (or null)
+    int32_t *deep_count;     // their number (device; zeroed before the launch)
+    int32_t kind;            // fitness kind (kFit*); kFitMse writes out, the others fit
+    int32_t max_score;       // M of the paper's fitness functions
+    double tax;              // length tax per token
+    beagle_fit_result *fit;  // [P] results of the paper's fitness functions
 };
 
 template <int MAXJ>
@@ -66,7 +105,7 @@ struct LaunchParams {
     int32_t xbuf_floats;     // floats per X stage buffer (max rows x tile)
     uint64_t wait_limit_ns;  // bound of every mbarrier wait (after it: error word, exit)
     int32_t stall_producer;  // test hook: the producer publishes nothing, so waits run out
-    int32_t pad_;
+    int32_t deep_pass;       // 1: this launch scores the jobs' deep lists (a 32-value stack)
 };
 
 // Error word bits

@@ -45,10 +45,12 @@ namespace beagle {
 // table on that token's handler id, which the packer stores in bits 24-28 of the current token
 // (so the branch does not wait for the load, whose latency the branch itself covers); the
 // program's END token leaves the loop.
-// The table has 32 entries (ids 21-31 end the program), so the 5-bit handler field needs no
-// clamp before the indexed branch.
+// The table has 32 entries (id 31 ends the program), so the 5-bit handler field needs no
+// clamp before the indexed branch. Ids 21-30 are the rest of Table 3 (POW and the
+// transcendentals leave the loop like sin; SIGN, CUBE and PASTE run here).
 #define BG_PTX_TBLPAD \
-    ", END_%=, END_%=, END_%=, END_%=, END_%=, END_%=, END_%=, END_%=, END_%=, END_%=, END_%="
+    ", POW_%=, SIGN_%=, CUBE_%=, CBRT_%=, TAN_%=, ASIN_%=, ACOS_%=, ATAN_%=, TANH_%=, " \
+    "PASTE_%=, END_%="
 #define BG_PTX_DISPATCH                                                                    \
     "shr.b32 h, %8, 24;\n\t"                                                               \
     "ld.shared.v2.u32 {%8, %9}, [%10];\n\t"                                                \
@@ -100,6 +102,30 @@ namespace beagle {
     BG_PTX_PDIV("%2", "%2", "a2") BG_PTX_PDIV("%3", "%3", "a3")                            \
     BG_PTX_TRACK4 BG_PTX_DISPATCH
 
+// The rest of Table 3: SIGN flips the four signs (|v| unchanged: nothing to track); CUBE is
+// (a a) a, each product rounded; PASTE pushes the top to its stack row, then loads the
+// register's row (its index in the constant word); POW and the transcendentals leave the loop.
+#define BG_PTX_EXT_BODY                                                                    \
+    "POW_%=:\n\tmov.u32 %11, 21;\n\tbra.uni OUT_%=;\n"                                      \
+    "CBRT_%=:\n\tmov.u32 %11, 24;\n\tbra.uni OUT_%=;\n"                                     \
+    "TAN_%=:\n\tmov.u32 %11, 25;\n\tbra.uni OUT_%=;\n"                                      \
+    "ASIN_%=:\n\tmov.u32 %11, 26;\n\tbra.uni OUT_%=;\n"                                     \
+    "ACOS_%=:\n\tmov.u32 %11, 27;\n\tbra.uni OUT_%=;\n"                                     \
+    "ATAN_%=:\n\tmov.u32 %11, 28;\n\tbra.uni OUT_%=;\n"                                     \
+    "TANH_%=:\n\tmov.u32 %11, 29;\n\tbra.uni OUT_%=;\n"                                     \
+    "SIGN_%=:\n\t"                                                                         \
+    "neg.f32 %0, %0;\n\tneg.f32 %1, %1;\n\tneg.f32 %2, %2;\n\tneg.f32 %3, %3;\n\t"          \
+    BG_PTX_DISPATCH                                                                        \
+    "CUBE_%=:\n\t"                                                                         \
+    "mul.rn.f32 a0, %0, %0;\n\tmul.rn.f32 a1, %1, %1;\n\t"                                 \
+    "mul.rn.f32 a2, %2, %2;\n\tmul.rn.f32 a3, %3, %3;\n\t"                                 \
+    "mul.rn.f32 %0, a0, %0;\n\tmul.rn.f32 %1, a1, %1;\n\t"                                 \
+    "mul.rn.f32 %2, a2, %2;\n\tmul.rn.f32 %3, a3, %3;\n\t"                                 \
+    BG_PTX_TRACK4 BG_PTX_DISPATCH                                                          \
+    "PASTE_%=:\n\t" BG_PTX_ROW BG_PTX_STROW                                                 \
+    "mad.lo.u32 rp, %9, 4, %13;\n\t" BG_PTX_LDROW("%0", "%1", "%2", "%3")                   \
+    BG_PTX_DISPATCH
+
 #define BG_PTX_INTERP4                                                                     \
     "{\n\t"                                                                                \
     ".reg .pred q;\n\t"                                                                    \
@@ -148,6 +174,7 @@ namespace beagle {
     BG_PTX_TRACK4 BG_PTX_DISPATCH                                                          \
     BG_PTX_ADDMUL_BODY                                                                     \
     BG_PTX_PDIVX_BODY                                                                      \
+    BG_PTX_EXT_BODY                                                                        \
     "END_%=:\n\tmov.u32 %11, 0;\n"                                                         \
     "OUT_%=:\n\t"                                                                          \
     "}"
@@ -158,7 +185,43 @@ static_assert(H_PUSHX == 0 && H_PUSHC == 1 && H_DUP == 2 && H_SWAP == 3 && H_DEL
                   H_ADDSUBX == 14 && H_MULX == 15 && H_PDIVX == 16 && H_ADDC == 17 &&
                   H_MULC == 18 && H_PDIVC == 19 && H_END == 20,
               "the PTX jump table lists the handlers in this order");
+static_assert(H_POW == 21 && H_SIGN == 22 && H_CUBE == 23 && H_CBRT == 24 && H_TAN == 25 &&
+                  H_ASIN == 26 && H_ACOS == 27 && H_ATAN == 28 && H_TANH == 29 &&
+                  H_PASTE == 30 && kNumHandlers == 31,
+              "the PTX jump table lists the rest of Table 3 in this order");
 static_assert(kBoxShift == 10, "the PTX loop hard-codes the input row shift");
+
+// Four values of a tensor-memory stack row (the warp's earlier stores are waited for).
+__device__ __forceinline__ void tmem_ld_row4(uint32_t addr, float &a0, float &a1, float &a2,
+                                             float &a3) {
+    asm volatile(
+        "tcgen05.wait::st.sync.aligned;\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%4];\n\t"
+        "tcgen05.wait::ld.sync.aligned;"
+        : "=f"(a0), "=f"(a1), "=f"(a2), "=f"(a3)
+        : "r"(addr)
+        : "memory");
+}
+
+// POW and the transcendentals of the rest of Table 3 on the 4 top values; tok is the token
+// that left the loop (POW's second operand is in its stack row).
+__device__ __forceinline__ void run_ext4(uint32_t code, uint32_t tok, uint32_t tstk, float &t0,
+                                         float &t1, float &t2, float &t3) {
+    using A = Arith<float>;
+    switch (code) {
+    case H_POW: {
+        float a0, a1, a2, a3;
+        tmem_ld_row4(tstk + 4u * ((tok >> 12) & 0xffu), a0, a1, a2, a3);
+        t0 = A::pow_(a0, t0); t1 = A::pow_(a1, t1); t2 = A::pow_(a2, t2); t3 = A::pow_(a3, t3);
+    } break;
+    case H_CBRT: t0 = A::cbrt_(t0); t1 = A::cbrt_(t1); t2 = A::cbrt_(t2); t3 = A::cbrt_(t3); break;
+    case H_TAN: t0 = A::tan_(t0); t1 = A::tan_(t1); t2 = A::tan_(t2); t3 = A::tan_(t3); break;
+    case H_ASIN: t0 = A::asin_(t0); t1 = A::asin_(t1); t2 = A::asin_(t2); t3 = A::asin_(t3); break;
+    case H_ACOS: t0 = A::acos_(t0); t1 = A::acos_(t1); t2 = A::acos_(t2); t3 = A::acos_(t3); break;
+    case H_ATAN: t0 = A::atan_(t0); t1 = A::atan_(t1); t2 = A::atan_(t2); t3 = A::atan_(t3); break;
+    default: t0 = A::tanh_(t0); t1 = A::tanh_(t1); t2 = A::tanh_(t2); t3 = A::tanh_(t3); break;
+    }
+}
 
 // prog: shared address of the packed program; xrow: shared address of this lane's first case
 // of input row 0; tstk: tensor-memory address of the warp's stack row 0 (4 columns a row).
@@ -177,16 +240,22 @@ __device__ __forceinline__ void run_program_ptx4(uint32_t prog, uint32_t xrow, u
                      : "r"(xrow), "r"(tstk)
                      : "memory");
         if (code == 0) break;
-        switch (code) {
-        case H_SIN:
-        case H_COS: sincos4(t0, t1, t2, t3, static_cast<int>(code) - H_SIN); break;
-        case H_EXP: t0 = A::exp_(t0); t1 = A::exp_(t1); t2 = A::exp_(t2); t3 = A::exp_(t3); break;
-        default: t0 = A::plog(t0); t1 = A::plog(t1); t2 = A::plog(t2); t3 = A::plog(t3); break;
+        if (code >= H_POW) {   // the rest of Table 3
+            run_ext4(code, cx, tstk, t0, t1, t2, t3);
+            // cbrt, atan and tanh of a valid value are valid; pow, tan, asin, acos may not be
+            if (code == H_CBRT || code == H_ATAN || code == H_TANH) continue;
+        } else {
+            switch (code) {
+            case H_SIN:
+            case H_COS: sincos4(t0, t1, t2, t3, static_cast<int>(code) - H_SIN); break;
+            case H_EXP: t0 = A::exp_(t0); t1 = A::exp_(t1); t2 = A::exp_(t2); t3 = A::exp_(t3); break;
+            default: t0 = A::plog(t0); t1 = A::plog(t1); t2 = A::plog(t2); t3 = A::plog(t3); break;
+            }
+            // sin, cos and the protected log of a valid value are finite and bounded (|ln|v||
+            // <= 69.1 for |v| <= 1e30), and an invalid operand was recorded when it was
+            // pushed, so only exp can produce a new invalid value here.
+            if (code != H_EXP) continue;
         }
-        // sin, cos and the protected log of a valid value are finite and bounded (|ln|v|| <=
-        // 69.1 for |v| <= 1e30), and an invalid operand was recorded when it was pushed, so
-        // only exp can produce a new invalid value here.
-        if (code != H_EXP) continue;
         m0 = A::track(m0, t0);
         m1 = A::track(m1, t1);
         m2 = A::track(m2, t2);
@@ -208,5 +277,6 @@ __device__ __forceinline__ void run_program_ptx4(uint32_t prog, uint32_t xrow, u
 #undef BG_PTX_TBLPAD
 #undef BG_PTX_PDIVX_BODY
 #undef BG_PTX_ADDMUL_BODY
+#undef BG_PTX_EXT_BODY
 
 }  // namespace beagle

@@ -34,7 +34,8 @@ namespace beagle {
     "mul.rn.f32 z, " NUM ", y;\n\tfma.rn.f32 e, nd, z, " NUM ";\n\t"                        \
     "fma.rn.f32 z, e, y, z;\n\tselp.f32 " DST ", z, 0f3F800000, q;\n\t"
 #define BG8_TBLPAD                                                                         \
-    ", END_%=, END_%=, END_%=, END_%=, END_%=, END_%=, END_%=, END_%=, END_%=, END_%=, END_%="
+    ", POW_%=, SIGN_%=, CUBE_%=, CBRT_%=, TAN_%=, ASIN_%=, ACOS_%=, ATAN_%=, TANH_%=, "   \
+    "PASTE_%=, END_%="
 // %0-%7 top of stack (8 cases), %8-%15 validity trackers, %16/%17 current token words, %18/%19
 // next token words (prefetched), %20 shared address of the token after that, %21 exit code,
 // %22 shared address of this lane's first case of input row 0 (half 0), %23 shared address of
@@ -96,6 +97,28 @@ namespace beagle {
 #define BG8_OP_ADD(D, L, R) "add.rn.f32 " D ", " L ", " R ";\n\t"
 #define BG8_OP_PDIV(D, L, R) BG8_PDIV(D, L, R)
 
+// The rest of Table 3 (as in interp_ptx.cuh): POW and the transcendentals leave the loop;
+// SIGN, CUBE ((a a) a) and PASTE (push the top, load the register's row) run here.
+#define BG8_EXT_BODY                                                                       \
+    "POW_%=:\n\tmov.u32 %21, 21;\n\tbra.uni OUT_%=;\n"                                      \
+    "CBRT_%=:\n\tmov.u32 %21, 24;\n\tbra.uni OUT_%=;\n"                                     \
+    "TAN_%=:\n\tmov.u32 %21, 25;\n\tbra.uni OUT_%=;\n"                                      \
+    "ASIN_%=:\n\tmov.u32 %21, 26;\n\tbra.uni OUT_%=;\n"                                     \
+    "ACOS_%=:\n\tmov.u32 %21, 27;\n\tbra.uni OUT_%=;\n"                                     \
+    "ATAN_%=:\n\tmov.u32 %21, 28;\n\tbra.uni OUT_%=;\n"                                     \
+    "TANH_%=:\n\tmov.u32 %21, 29;\n\tbra.uni OUT_%=;\n"                                     \
+    "SIGN_%=:\n\t"                                                                         \
+    "neg.f32 %0, %0;\n\tneg.f32 %1, %1;\n\tneg.f32 %2, %2;\n\tneg.f32 %3, %3;\n\t"          \
+    "neg.f32 %4, %4;\n\tneg.f32 %5, %5;\n\tneg.f32 %6, %6;\n\tneg.f32 %7, %7;\n\t"          \
+    BG8_DISPATCH                                                                           \
+    "CUBE_%=:\n\t"                                                                         \
+    "mul.rn.f32 a0, %0, %0;\n\tmul.rn.f32 a1, %1, %1;\n\tmul.rn.f32 a2, %2, %2;\n\t"        \
+    "mul.rn.f32 a3, %3, %3;\n\tmul.rn.f32 a4, %4, %4;\n\tmul.rn.f32 a5, %5, %5;\n\t"        \
+    "mul.rn.f32 a6, %6, %6;\n\tmul.rn.f32 a7, %7, %7;\n\t"                                 \
+    BG8_MAP(BG8_OP_MUL, , BG8_A, BG8_T) BG8_TRACK8 BG8_DISPATCH                            \
+    "PASTE_%=:\n\t" BG8_ROW BG8_ST_TOP("rp")                                                \
+    "mad.lo.u32 rp, %17, 1024, %23;\n\t" BG8_LD_TOP("rp") BG8_DISPATCH
+
 #define BG_PTX_INTERP8                                                                     \
     "{\n\t"                                                                                \
     ".reg .pred q;\n\t"                                                                    \
@@ -142,6 +165,7 @@ namespace beagle {
     "PDIVX_%=:\n\t" BG8_XA BG8_LD_A("xa") "bra.uni DIVTA_%=;\n"                              \
     "PDIVC_%=:\n\t" BG8_S BG8_SET_A_S                                                      \
     "DIVTA_%=:\n\t" BG8_MAP(BG8_OP_PDIV, , BG8_T, BG8_A) BG8_TRACK8 BG8_DISPATCH           \
+    BG8_EXT_BODY                                                                           \
     "END_%=:\n\tmov.u32 %21, 0;\n"                                                         \
     "OUT_%=:\n\t"                                                                          \
     "}"
@@ -180,7 +204,25 @@ __device__ __forceinline__ void run_program_ptx8(uint32_t prog, uint32_t xrow, u
         for (int hh = 0; hh < 2; ++hh) {
             float u0 = hh ? t4 : t0, u1 = hh ? t5 : t1, u2 = hh ? t6 : t2, u3 = hh ? t7 : t3;
             float n0 = hh ? m4 : m0, n1 = hh ? m5 : m1, n2 = hh ? m6 : m2, n3 = hh ? m7 : m3;
-            switch (code) {
+            if (code >= H_POW) {   // the rest of Table 3
+                if (code == H_POW) {   // second operand: this half of the token's stack row
+                    float a0, a1, a2, a3;
+                    lds4(stk + ((cx >> 12) & 0xffu) * 1024u + 512u * hh, a0, a1, a2, a3);
+                    u0 = A::pow_(a0, u0); u1 = A::pow_(a1, u1);
+                    u2 = A::pow_(a2, u2); u3 = A::pow_(a3, u3);
+                } else {
+                    switch (code) {
+                    case H_CBRT: u0 = A::cbrt_(u0); u1 = A::cbrt_(u1); u2 = A::cbrt_(u2); u3 = A::cbrt_(u3); break;
+                    case H_TAN: u0 = A::tan_(u0); u1 = A::tan_(u1); u2 = A::tan_(u2); u3 = A::tan_(u3); break;
+                    case H_ASIN: u0 = A::asin_(u0); u1 = A::asin_(u1); u2 = A::asin_(u2); u3 = A::asin_(u3); break;
+                    case H_ACOS: u0 = A::acos_(u0); u1 = A::acos_(u1); u2 = A::acos_(u2); u3 = A::acos_(u3); break;
+                    case H_ATAN: u0 = A::atan_(u0); u1 = A::atan_(u1); u2 = A::atan_(u2); u3 = A::atan_(u3); break;
+                    default: u0 = A::tanh_(u0); u1 = A::tanh_(u1); u2 = A::tanh_(u2); u3 = A::tanh_(u3); break;
+                    }
+                }
+                n0 = A::track(n0, u0); n1 = A::track(n1, u1);
+                n2 = A::track(n2, u2); n3 = A::track(n3, u3);
+            } else switch (code) {
             case H_SIN:
             case H_COS: sincos4(u0, u1, u2, u3, static_cast<int>(code) - H_SIN); break;
             case H_PLOG:
@@ -215,5 +257,6 @@ __device__ __forceinline__ void run_program_ptx8(uint32_t prog, uint32_t xrow, u
 #undef BG8_LD_A
 #undef BG8_MAP
 #undef BG8_SET_A_S
+#undef BG8_EXT_BODY
 
 }  // namespace beagle

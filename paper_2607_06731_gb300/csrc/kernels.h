@@ -25,7 +25,8 @@ inline int tile_for(int precision, int cases, int requested) {
     return requested ? requested : 512;
 }
 constexpr int kCasesFp64 = 2;              // fitness cases per lane per pass, FP64 path
-constexpr size_t kSmemBudget = 227 * 1024; // dynamic shared memory per CTA
+// Dynamic shared memory per CTA: 227 KB less room for the kernel's static work table.
+constexpr size_t kSmemBudget = 225 * 1024;
 
 // Dynamic shared memory of one CTA with nw consumer warps and `cases` cases per lane.
 size_t smem_bytes(int precision, int cases, int xbuf_floats, int tile, int nw);
@@ -56,5 +57,8 @@ cudaError_t launch_score_batch(const LaunchParams<kMaxJobs> &prm, int precision,
 // Load every scoring and finalize kernel instantiation (module loading is lazy), so that a
 // later stream capture makes no loader calls.
 cudaError_t load_kernels();
+// The deep pass (32-value stack) over one job's deep list, then the finalize of every program
+// of the job (the serving loop's path for programs deeper than its kernel's stack).
+cudaError_t launch_deep_and_finalize(const LaunchParams<1> &prm, int precision, cudaStream_t s);
 
 }  // namespace beagle

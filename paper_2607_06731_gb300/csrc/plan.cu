@@ -69,23 +69,25 @@ beagle_status enqueue(const std::vector<Planned> &jobs, size_t b, size_t e, int 
                       bool sort, cudaStream_t s) {
     LaunchParams<MAXJ> prm;
     std::memset(&prm, 0, sizeof prm);
-    size_t scratch = 256;
+    // header (work counters, error word, deep counts), then per job: partials, the
+    // length order (when sorting) and the list of programs deeper than the fast pass's stack
+    size_t scratch = kHdrBytes;
     for (size_t i = b; i < e; ++i) {
-        scratch += up256(jobs[i].part_bytes);
+        scratch += up256(jobs[i].part_bytes) + up256(sizeof(int32_t) * jobs[i].dev.P);
         if (sort && !jobs[i].dev.order) scratch += up256(sizeof(int32_t) * jobs[i].dev.P);
     }
     char *base = nullptr;
     cudaError_t err = cudaMallocAsync(reinterpret_cast<void **>(&base), scratch, s);
     if (err != cudaSuccess)
         return fail(BEAGLE_ERR_OOM, "scratch of %zu bytes: %s", scratch, cudaGetErrorString(err));
-    err = cudaMemsetAsync(base, 0, 256, s);
+    err = cudaMemsetAsync(base, 0, kHdrBytes, s);
     if (err != cudaSuccess) {
         cudaFreeAsync(base, s);
         return cuda_fail(err, "scratch memset");
     }
-    prm.counter = reinterpret_cast<unsigned int *>(base);
-    prm.error = reinterpret_cast<unsigned int *>(base + 128);
-    char *cur = base + 256;
+    prm.counter = reinterpret_cast<unsigned int *>(base + kHdrCounter);
+    prm.error = reinterpret_cast<unsigned int *>(base + kHdrError);
+    char *cur = base + kHdrBytes;
     int64_t items = 0;
     int nj = 0;
     OrderParams op;
@@ -95,6 +97,9 @@ beagle_status enqueue(const std::vector<Planned> &jobs, size_t b, size_t e, int 
         prm.jobs[nj] = jobs[i].dev;
         prm.jobs[nj].partials = reinterpret_cast<uint32_t *>(cur);
         cur += up256(jobs[i].part_bytes);
+        prm.jobs[nj].deep_list = reinterpret_cast<int32_t *>(cur);
+        prm.jobs[nj].deep_count = reinterpret_cast<int32_t *>(base + kHdrDeep) + nj;
+        cur += up256(sizeof(int32_t) * jobs[i].dev.P);
         if (sort && !jobs[i].dev.order) {
             int32_t *ord = reinterpret_cast<int32_t *>(cur);
             cur += up256(sizeof(int32_t) * jobs[i].dev.P);
@@ -146,8 +151,13 @@ beagle_status score_jobs(const JobRequest *reqs, int n, int precision, cudaStrea
             return fail(BEAGLE_ERR_DATASET, "job %d: dataset %d lives on device %d, current is %d",
                         i, r.dataset_id, ds->device, dev);
         if (r.P == 0) continue;
-        if (!r.programs || !r.offsets || !r.lengths || !r.consts || !r.out)
+        if (!r.programs || !r.offsets || !r.lengths || !r.consts ||
+            (r.kind == kFitMse ? !r.out : !r.fit))
             return fail(BEAGLE_ERR_ARG, "job %d: null pointer argument", i);
+        if (r.kind == kFitMse && ds->invalid_targets)
+            return fail(BEAGLE_ERR_DATASET,
+                        "job %d: dataset %d holds invalid targets; score it with "
+                        "beagle_score_fit", i, r.dataset_id);
         Planned pj;
         std::memset(&pj, 0, sizeof pj);
         pj.dev.ops = r.programs;
@@ -163,6 +173,10 @@ beagle_status score_jobs(const JobRequest *reqs, int n, int precision, cudaStrea
         pj.dev.rows = ds->rows;
         pj.dev.ybar = ds->ybar;
         pj.dev.syy = precision == BEAGLE_FP64 ? ds->syy : ds->syy32;
+        pj.dev.kind = r.kind;
+        pj.dev.max_score = r.max_score;
+        pj.dev.tax = r.tax;
+        pj.dev.fit = r.fit;
         pj.map = &ds->map;
         keep.push_back(ds);
         jobs.push_back(pj);
@@ -223,7 +237,8 @@ beagle_status score_jobs(const JobRequest *reqs, int n, int precision, cudaStrea
             JobDev &J = lj[i].dev;
             J.tiles = static_cast<int32_t>((J.N + tile - 1) / tile);
             J.tile_sy = precision == BEAGLE_FP64 ? lds[i]->tile_sy64[which] : lds[i]->tile_sy[which];
-            lj[i].part_bytes = static_cast<size_t>(kNumFields) * J.tiles * J.P * sizeof(uint32_t);
+            lj[i].part_bytes = static_cast<size_t>(J.kind == kFitMse ? kNumFields : kNumFitFields) *
+                               J.tiles * J.P * sizeof(uint32_t);
             work += J.P * J.tiles;
         }
         int group = plan_group(work, nw, grid);

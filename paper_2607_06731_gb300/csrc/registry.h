@@ -23,6 +23,7 @@ struct Dataset {
     CUtensorMap map;                          // box: 256 cases x rows
     double ybar = 0.0, syy = 0.0;
     double syy32 = 0.0;                         // sum of squares of the stored fp32 y - ybar
+    bool invalid_targets = false;               // y may hold invalid targets (fit kinds only)
     int holds = 0;                            // serving runs that keep it resident
     ~Dataset();
 };
@@ -42,6 +43,10 @@ struct JobRequest {
     beagle_fitness *out;
     const int32_t *order;   // optional device permutation of [0, P), may be null
     void *fout;             // optional device [P][N] per-case outputs, may be null
+    int32_t kind = 0;       // fitness kind (BEAGLE_FIT_*); MSE_R2 writes out, others fit
+    int32_t max_score = 0;  // M of the paper's fitness functions
+    double tax = 0.0;       // length tax per token (resolved: >= 0)
+    beagle_fit_result *fit = nullptr;
 };
 
 // Launch-shape overrides (0 = choose automatically).

@@ -1,0 +1,871 @@
+// Device code shared by the scoring kernels (score_kernels.cu) and the serving kernel
+// (serve_kernels.cu): shared-memory layout, per-(program, tile) evaluation and tile
+// statistics, and the per-program fp64 merge of the tiles (the finalize step).
+#pragma once
+
+#include "interp_ptx.cuh"
+#include "interp_ptx8.cuh"
+#include "kernels.h"
+#include "score.cuh"
+
+namespace beagle {
+
+// Shared-memory layout of one CTA (dynamic), nw consumer warps:
+//   [0, 64)        mbarriers: full[2], empty[2]
+//   [64, 128)      slot descriptors (2 x Slot)
+//   [128, ...)     X stage buffers: 2 x xbuf_floats fp32 (TMA destinations, 128-byte aligned)
+//   ...            per-warp output buffers: nw x tile x T (none on the 8-case FP32 path)
+//   ...            per-warp packed programs: nw x (kMaxLen + 2) x uint2
+//   ...            per-warp value stacks: nw x (kMaxDepth - 1) rows x 32 K x T
+struct Slot {
+    int job;        // -1: no more work
+    int tile;
+    int group;
+    int next;       // next program of the item (shared-memory counter)
+};
+
+// Tensor memory (TMEM): allocation of ncols columns (a power of two, 32..512) by one whole
+// warp, the base address written to *dst in shared memory; the same warp frees it. The fences
+// order TMEM accesses around the CTA barriers that publish the address and end its use.
+__device__ __forceinline__ void tmem_alloc(uint32_t *dst, uint32_t ncols) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                 ::"r"(smem_addr(dst)), "r"(ncols) : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr),
+                 "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void tmem_fence_before_sync() {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_fence_after_sync() {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+// The 4-case FP32 path keeps its stack rows in tensor memory (64 columns a warp, the warp's
+// 32-lane quarter of TMEM being warp % 4 and its column slot warp / 4); the other paths keep
+// them in shared memory.
+template <typename T, int K>
+constexpr bool kTmemStackPath = sizeof(T) == 4 && K == 4;
+// Columns a warp's stack takes: D - 1 rows of 4 columns, rounded to a power of two (64 for
+// the 16-value fast pass, 128 for the 32-value deep pass: 16 warps fill the 512 columns).
+__host__ __device__ constexpr int tmem_cols_per_warp(int D) { return D <= 16 ? 64 : 128; }
+static_assert(4 * (kDepthFast - 1) <= tmem_cols_per_warp(kDepthFast), "rows fit the columns");
+static_assert(4 * (kMaxDepth - 1) <= tmem_cols_per_warp(kMaxDepth), "rows fit the columns");
+__host__ __device__ constexpr uint32_t tmem_columns(int nw, int D) {   // power of two, 32..512
+    const int need = (nw + 3) / 4 * tmem_cols_per_warp(D);
+    return need <= 32 ? 32u : need <= 64 ? 64u : need <= 128 ? 128u : need <= 256 ? 256u : 512u;
+}
+
+template <typename T, int K, int D>
+struct SmemLayout {
+    static constexpr size_t kStackRows = D - 1;
+    static constexpr bool kTmemStack = kTmemStackPath<T, K>;
+    static __host__ __device__ size_t xbuf_off() { return 128; }
+    static __host__ __device__ size_t fbuf_off(int xbuf_floats) {
+        return xbuf_off() + 2ull * xbuf_floats * sizeof(float);
+    }
+    static __host__ __device__ size_t pbuf_off(int xbuf_floats, int tile, int nw) {
+        return fbuf_off(xbuf_floats) +
+               (sizeof(T) == 4 && K == 8 ? 0 : static_cast<size_t>(nw) * tile * sizeof(T));
+    }
+    static __host__ __device__ size_t stack_off(int xbuf_floats, int tile, int nw) {
+        return pbuf_off(xbuf_floats, tile, nw) + static_cast<size_t>(nw) * (kMaxLen + 2) * sizeof(uint2);
+    }
+    static __host__ __device__ size_t stack_bytes_per_warp() {
+        return kTmemStack ? 0 : kStackRows * 32 * K * sizeof(T);
+    }
+    static __host__ __device__ size_t total(int xbuf_floats, int tile, int nw) {
+        return stack_off(xbuf_floats, tile, nw) + static_cast<size_t>(nw) * stack_bytes_per_warp();
+    }
+};
+
+// The 8-case FP32 path runs one 256-case tile per pass and keeps the outputs in registers;
+// the other paths write them to the warp's shared-memory buffer.
+template <typename T, int K>
+constexpr bool kOutputsInRegs = sizeof(T) == 4 && K == 8;
+
+// A tile's outputs in the order the statistics read them: lane l's values are the cases
+// 128 h + 4 l + j (h over the tile's 128-case halves, j = 0..3), the order in which the 8-case
+// path holds them, so every path forms the same sums in the same order.
+template <typename T, int K>
+struct TileValues {
+    T r[kOutputsInRegs<T, K> ? 8 : 1];
+    const T *buf;
+    // values 4h..4h+3 of this lane (h a compile-time index on the register path)
+    __device__ __forceinline__ void get4(int h, int lane, T (&v)[4]) const {
+        if constexpr (kOutputsInRegs<T, K>) {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) v[j] = r[4 * h + j];
+        } else if constexpr (sizeof(T) == 4) {
+            const float4 q = *reinterpret_cast<const float4 *>(buf + h * 128 + lane * 4);
+            v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+        } else {
+            const double2 *src = reinterpret_cast<const double2 *>(buf + h * 128 + lane * 4);
+            const double2 a = src[0], b = src[1];
+            v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+        }
+    }
+    // f(h, v) for every 128-case half of the tile that holds cases
+    template <typename F>
+    __device__ __forceinline__ void for_halves(int halves, int lane, F &&f) const {
+        if constexpr (kOutputsInRegs<T, K>) {
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                if (h < halves) {
+                    T v[4];
+                    get4(h, lane, v);
+                    f(h, v);
+                }
+            }
+        } else {
+#pragma unroll 1
+            for (int h = 0; h < halves; ++h) {
+                T v[4];
+                get4(h, lane, v);
+                f(h, v);
+            }
+        }
+    }
+};
+
+// ------------------------------------------------------------------ the paper's fitness
+// Rows of the staged tile: lane l reads the 4 consecutive cases 128 h + 4 l .. + 3 of a row.
+__device__ __forceinline__ float4 tile_row4(const float *row, int h, int lane, int rows) {
+    const int i = h * 128 + lane * 4;
+    return *reinterpret_cast<const float4 *>(row + (i / kBox) * rows * kBox + (i % kBox));
+}
+__device__ __forceinline__ float f4_elem(const float4 &v, int j) {
+    return j == 0 ? v.x : j == 1 ? v.y : j == 2 ? v.z : v.w;
+}
+
+__device__ __forceinline__ long long warp_sum_i64(long long v) {
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    return v;
+}
+
+// Eq. 5's per-case reward of a valid pair, in the path's precision, each operation rounded
+// once (no contraction): q = min/max of the magnitudes, q^k (k = 1, 2, 3, 8), M q^k, minus
+// M/11 when the two have opposite signs, rounded to nearest even.
+__device__ __forceinline__ long long std_reward(float f, float y, int k, int M) {
+    const float a = fabsf(f), b = fabsf(y);
+    const float mx = fmaxf(a, b), mn = fminf(a, b);
+    if (mx == 0.0f) return M;
+    const float q = __fdiv_rn(mn, mx);
+    float qk = q;
+    if (k == 2) qk = __fmul_rn(q, q);
+    else if (k == 3) qk = __fmul_rn(__fmul_rn(q, q), q);
+    else if (k == 8) {
+        const float q2 = __fmul_rn(q, q), q4 = __fmul_rn(q2, q2);
+        qk = __fmul_rn(q4, q4);
+    }
+    const float Mf = static_cast<float>(M);
+    float v = __fmul_rn(Mf, qk);
+    if ((f < 0.0f && y > 0.0f) || (f > 0.0f && y < 0.0f)) v = __fsub_rn(v, __fdiv_rn(Mf, 11.0f));
+    return static_cast<long long>(rintf(v));
+}
+__device__ __forceinline__ long long std_reward(double f, float yf, int k, int M) {
+    const double y = static_cast<double>(yf);
+    const double a = fabs(f), b = fabs(y);
+    const double mx = fmax(a, b), mn = fmin(a, b);
+    if (mx == 0.0) return M;
+    const double q = __ddiv_rn(mn, mx);
+    double qk = q;
+    if (k == 2) qk = __dmul_rn(q, q);
+    else if (k == 3) qk = __dmul_rn(__dmul_rn(q, q), q);
+    else if (k == 8) {
+        const double q2 = __dmul_rn(q, q), q4 = __dmul_rn(q2, q2);
+        qk = __dmul_rn(q4, q4);
+    }
+    const double Md = static_cast<double>(M);
+    double v = __dmul_rn(Md, qk);
+    if ((f < 0.0 && y > 0.0) || (f > 0.0 && y < 0.0)) v = __dsub_rn(v, __ddiv_rn(Md, 11.0));
+    return static_cast<long long>(rint(v));
+}
+
+template <typename T>
+__device__ __forceinline__ void put_value(uint32_t *w, T v) {
+    if constexpr (sizeof(T) == 4) {
+        w[0] = __float_as_uint(v);
+        w[1] = 0u;
+    } else {
+        const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(v));
+        w[0] = static_cast<uint32_t>(b);
+        w[1] = static_cast<uint32_t>(b >> 32);
+    }
+}
+
+// Tile statistics of the paper's fitness functions. Invalid cases arrive as NaN outputs (a
+// valid value is never NaN); all_bad: a constant of the program is itself invalid, so every
+// case is. Targets are valid when |y| <= 1e30 (NaN fails).
+template <typename T, int K, typename Vals, typename FieldFn>
+__device__ __forceinline__ void fit_tile_stats(const JobDev &J, int nval, bool all_bad,
+                                            const Vals &vals, const float *xs, int lane,
+                                            FieldFn field) {
+    const int halves = (nval + 127) / 128;
+    const int rows = J.rows;
+    const float *yrow = xs + J.d * kBox;
+    const float *ycrow = xs + (J.d + 1) * kBox;
+    uint32_t c1 = 0, c2 = 0, n = 0;
+    uint32_t w[kNumFitFields];
+#pragma unroll
+    for (int f = 0; f < kNumFitFields; ++f) w[f] = 0u;
+    if (J.kind == kFitCorr) {
+        using Sum = typename SumOf<T>::type;
+        Sum sf;
+        const T inf = static_cast<T>(INFINITY);
+        T fabsmax = T(0), fmn = inf, fmx = -inf;
+        float ymn = INFINITY, ymx = -INFINITY, ycmax = 0.0f;
+        vals.for_halves(halves, lane, [&](int h, const T (&v)[4]) {
+            const float4 y4 = tile_row4(yrow, h, lane, rows);
+            const float4 yc4 = tile_row4(ycrow, h, lane, rows);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                if (h * 128 + lane * 4 + j < nval) {
+                    const T fi = v[j];
+                    const float yv = f4_elem(y4, j);
+                    const bool fv = !all_bad && fi == fi, tv = fabsf(yv) <= 1e30f;
+                    c1 += fv != tv;
+                    c2 += !fv && !tv;
+                    if (fv && tv) {
+                        ++n;
+                        sf.add(fi);
+                        fabsmax = fmax(fabsmax, fabs(fi));
+                        fmn = fmin(fmn, fi);
+                        fmx = fmax(fmx, fi);
+                        ymn = fminf(ymn, yv);
+                        ymx = fmaxf(ymx, yv);
+                        ycmax = fmaxf(ycmax, fabsf(f4_elem(yc4, j)));
+                    }
+                }
+            }
+        });
+        n = __reduce_add_sync(kFull, n);
+        c1 = __reduce_add_sync(kFull, c1);
+        c2 = __reduce_add_sync(kFull, c2);
+        sf.warp_allreduce();
+#pragma unroll
+        for (int o = 16; o >= 1; o >>= 1) {
+            fabsmax = fmax(fabsmax, __shfl_xor_sync(kFull, fabsmax, o));
+            fmn = fmin(fmn, __shfl_xor_sync(kFull, fmn, o));
+            fmx = fmax(fmx, __shfl_xor_sync(kFull, fmx, o));
+            ymn = fminf(ymn, __shfl_xor_sync(kFull, ymn, o));
+            ymx = fmaxf(ymx, __shfl_xor_sync(kFull, ymx, o));
+            ycmax = fmaxf(ycmax, __shfl_xor_sync(kFull, ycmax, o));
+        }
+        T m = T(0);
+        if constexpr (sizeof(T) == 4) m = n ? (sf.s + sf.c) / static_cast<float>(n) : 0.0f;
+        else m = n ? sf.s / static_cast<double>(n) : 0.0;
+        int kd = 0, ky = 0;
+        T sds = T(1), sys = T(1);
+        if constexpr (sizeof(T) == 4) {   // valid values reach 1e30: scale the fp32 sums
+            kd = scale_exponent(2.0f * fabsmax);
+            ky = scale_exponent(ycmax);
+            sds = pow2f(-kd);
+            sys = pow2f(-ky);
+        }
+        Sum sd, sdd, sdy, sy, syy;
+        vals.for_halves(halves, lane, [&](int h, const T (&v)[4]) {
+            const float4 y4 = tile_row4(yrow, h, lane, rows);
+            const float4 yc4 = tile_row4(ycrow, h, lane, rows);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                if (h * 128 + lane * 4 + j < nval) {
+                    const T fi = v[j];
+                    const float yv = f4_elem(y4, j);
+                    if (!all_bad && fi == fi && fabsf(yv) <= 1e30f) {
+                        const T dv = (fi - m) * sds;
+                        // FP32: the stored fp32 y - ybar; FP64: y - ybar formed in fp64
+                        const T yc = (sizeof(T) == 4 ? static_cast<T>(f4_elem(yc4, j))
+                                                     : static_cast<T>(yv) - static_cast<T>(J.ybar)) *
+                                     sys;
+                        sd.add(dv);
+                        sdd.add_prod(dv, dv);
+                        sdy.add_prod(dv, yc);
+                        sy.add(yc);
+                        syy.add_prod(yc, yc);
+                    }
+                }
+            }
+        });
+        sd.warp_allreduce();
+        sdd.warp_allreduce();
+        sdy.warp_allreduce();
+        sy.warp_allreduce();
+        syy.warp_allreduce();
+        if (lane == 0) {
+            put_value<T>(w + kfMean, m);
+            put_pair(w + kfSd, sd);
+            put_pair(w + kfSdd, sdd);
+            put_pair(w + kfSdy, sdy);
+            put_pair(w + kfSy, sy);
+            put_pair(w + kfSyy, syy);
+            put_value<T>(w + kfFmin, fmn);
+            put_value<T>(w + kfFmax, fmx);
+            w[kfYmin] = __float_as_uint(ymn);
+            w[kfYmax] = __float_as_uint(ymx);
+            w[kfFlags] = (static_cast<uint32_t>(kd) << 16) | (static_cast<uint32_t>(ky) << 24);
+        }
+    } else {
+        const int k = J.kind == kFitStd ? 1 : J.kind == kFitStd + 1 ? 2 :
+                      J.kind == kFitStd + 2 ? 3 : 8;
+        const int M = J.max_score;
+        long long score = 0;
+        vals.for_halves(halves, lane, [&](int h, const T (&v)[4]) {
+            const float4 y4 = tile_row4(yrow, h, lane, rows);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                if (h * 128 + lane * 4 + j < nval) {
+                    const T fi = v[j];
+                    const float yv = f4_elem(y4, j);
+                    const bool fv = !all_bad && fi == fi, tv = fabsf(yv) <= 1e30f;
+                    c1 += fv != tv;
+                    c2 += !fv && !tv;
+                    if (J.kind == kFitValidate) {
+                        if (fv && tv &&
+                            fabs(static_cast<double>(fi) - static_cast<double>(yv)) <=
+                                0.001 * fabs(static_cast<double>(yv)))
+                            ++score;
+                    } else if (fv && tv) {
+                        score += std_reward(fi, yv, k, M);
+                    } else {
+                        score += (fv || tv) ? -M : M;
+                    }
+                }
+            }
+        });
+        score = warp_sum_i64(score);
+        c1 = __reduce_add_sync(kFull, c1);
+        c2 = __reduce_add_sync(kFull, c2);
+        if (lane == 0) {
+            w[kfScore] = static_cast<uint32_t>(static_cast<unsigned long long>(score));
+            w[kfScore + 1] = static_cast<uint32_t>(static_cast<unsigned long long>(score) >> 32);
+        }
+    }
+    if (lane == 0) {
+        w[kfN] = n;
+        w[kfC1] = c1;
+        w[kfC2] = c2;
+#pragma unroll
+        for (int f = 0; f < kNumFitFields; ++f) *field(f) = w[f];
+    }
+    __syncwarp();
+}
+
+// Score program p on tile t: the partials of (p, t) are written. Returns 1 instead when the
+// program is deeper than this kernel's stack and was left to the deep pass (its partials are
+// not written here), else 0.
+template <typename T, int K, int D>
+__device__ __forceinline__ int process_program(const JobDev &J, int64_t p, int t, int tile,
+                                                const float *xs, uint2 *pbuf, T *fbuf, T *stk,
+                                                uint32_t tstk, int lane) {
+    using Sum = typename SumOf<T>::type;
+    constexpr bool kRegs = kOutputsInRegs<T, K>;
+    constexpr int CH = 32 * K;
+    const int64_t off = J.offs[p];
+    const int L = J.lens[p];
+    const Packed pk = pack_program<T, D>(J.ops + off, J.consts + off, L, J.d, pbuf, lane);
+    if (pk.deep) {
+        // Deeper than this pass's stack: the deep pass scores it. The warp that meets the
+        // program's first tile enqueues it once; without a deep list it cannot be scored.
+        if (J.deep_list) {
+            if (t == 0 && lane == 0) J.deep_list[atomicAdd(J.deep_count, 1)] = static_cast<int32_t>(p);
+            return 1;
+        }
+    }
+    if constexpr (sizeof(T) == 4 && K == 4) {
+        // Bits 24-28 of each token: the handler id of the token after it (the 4-case
+        // interpreter branches on it while it loads that token). Each round reads, then writes.
+        for (int base = 0; base < pk.n; base += 32) {
+            const int i = base + lane;
+            const uint32_t nh = i < pk.n ? (pbuf[i + 1].x & 31u) : 0u;
+            __syncwarp();
+            if (i < pk.n) pbuf[i].x |= nh << 24;
+            __syncwarp();
+        }
+    }
+
+    const int64_t P = J.P;
+    const int tiles = J.tiles;
+    uint32_t *part = J.partials;
+    auto field = [&](int f) -> uint32_t * {
+        return part + (static_cast<int64_t>(f) * tiles + t) * P + p;
+    };
+    if (pk.malformed || pk.deep) {
+        if (lane == 0) *field(J.kind == kFitMse ? kTileFlags : kfFlags) = TF_MALFORMED;
+        return 0;
+    }
+    const int64_t tstart = static_cast<int64_t>(t) * tile;
+    const int nval = static_cast<int>(min(static_cast<int64_t>(tile), J.N - tstart));
+    const int rows = J.rows;
+
+    TileValues<T, K> vals;
+    vals.buf = fbuf;
+    bool anybad = pk.const_bad;
+    if constexpr (kRegs) {   // one pass: the whole 256-case tile
+        bool bad[8];
+        run_program_ptx8(smem_addr(pbuf), smem_addr(xs + lane * 4), smem_addr(stk + lane * 4),
+                         vals.r, bad);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            if (bad[j] && (j >> 2) * 128 + lane * 4 + (j & 3) < nval) anybad = true;
+            if (J.kind != kFitMse && bad[j]) vals.r[j] = __int_as_float(0x7fc00000);
+        }
+    } else {
+        for (int c0 = 0; c0 < nval; c0 += CH) {
+            const float *xrow = xs + (c0 / kBox) * rows * kBox + (c0 % kBox) + lane * K;
+            T f[K];
+            bool bad[K];
+            if constexpr (sizeof(T) == 4 && K == 4)
+                run_program_ptx4(smem_addr(pbuf), smem_addr(xrow), tstk, f, bad);
+            else
+                run_program<T, K>(smem_addr(pbuf), pk.n, smem_addr(xrow),
+                                  smem_addr(stk + lane * K), f, bad);
+            if (J.kind != kFitMse) {   // the paper's fitness: invalid cases become NaN
+#pragma unroll
+                for (int j = 0; j < K; ++j)
+                    if (bad[j]) f[j] = static_cast<T>(__int_as_float(0x7fc00000));
+            }
+            sts_vec<T, K>(smem_addr(fbuf + c0 + lane * K), f);
+#pragma unroll
+            for (int j = 0; j < K; ++j)
+                if (bad[j] && c0 + lane * K + j < nval) anybad = true;
+        }
+    }
+    anybad = __any_sync(kFull, anybad);
+    __syncwarp();
+    const int halves = (nval + 127) / 128;
+    if (J.fout) {   // per-case outputs requested (beagle_eval)
+        T *dst = static_cast<T *>(J.fout) + p * J.N + tstart;
+        vals.for_halves(halves, lane, [&](int h, const T (&v)[4]) {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int i = h * 128 + lane * 4 + j;
+                if (i < nval) dst[i] = v[j];
+            }
+        });
+    }
+    if (J.kind != kFitMse) {
+        fit_tile_stats<T, K>(J, nval, pk.const_bad, vals, xs, lane, field);
+        return 0;
+    }
+    if (anybad) {
+        if (lane == 0) *field(kTileFlags) = TF_INVALID;
+        return 0;
+    }
+
+    // Tile statistics. Lane l's targets for half h are 4 consecutive floats. The general form
+    // (FP64 path; FP32 when the one-pass sums overflow) takes two passes over the tile's
+    // outputs: the tile mean first, then sums centred on it. Valid values reach 1e30, so on the
+    // FP32 path each sum is taken over terms scaled by an exact power of two 2^-k (k = 0 unless
+    // the tile holds values above 2^50); the finalize kernel multiplies back in fp64.
+    const float *yrow = xs + J.d * kBox;          // target row
+    const float *ycrow = xs + (J.d + 1) * kBox;   // centred-target row
+    auto row4 = [&](const float *row, int h) {
+        const int i = h * 128 + lane * 4;
+        return *reinterpret_cast<const float4 *>(row + (i / kBox) * rows * kBox + (i % kBox));
+    };
+    auto elem = [](const float4 &v, int j) {
+        return j == 0 ? v.x : j == 1 ? v.y : j == 2 ? v.z : v.w;
+    };
+    if constexpr (sizeof(T) == 4) {
+        // One pass, around the mean m0 of the tile's first 128 outputs: the finalize merge
+        // cancels about as little around m0 as around the tile mean. sum e^2 has positive terms
+        // only and is a plain fp32 sum (relative error below 22 u: 16 terms a lane, then 5
+        // pairwise steps); the centred sums are compensated. An overflow anywhere in these
+        // unscaled sums leaves an infinity or a NaN in them; then the two-pass form below,
+        // which scales the terms, runs instead (outputs or targets near 2^60 and above). The
+        // outputs are all equal exactly when the sum of |f - f_0| is 0 (no flush to zero).
+        float h0[4];
+        vals.get4(0, lane, h0);
+        const int n0 = min(nval, 128);
+        float s0 = 0.0f;
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            if (lane * 4 + j < n0) s0 += h0[j];
+#pragma unroll
+        for (int o = 16; o >= 1; o >>= 1) s0 += __shfl_xor_sync(kFull, s0, o);
+        const float m0 = s0 / static_cast<float>(n0);
+        const float fa = __shfl_sync(kFull, h0[0], 0);
+        float se1 = 0.0f, ad = 0.0f;
+        KahanF sd1, sdd1, sdy1;
+        vals.for_halves(halves, lane, [&](int h, const T (&v)[4]) {
+            const float4 y4 = row4(yrow, h);
+            const float4 yc4 = row4(ycrow, h);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                if (h * 128 + lane * 4 + j < nval) {
+                    const float fi = v[j];
+                    const float e = fi - elem(y4, j);
+                    se1 = fmaf(e, e, se1);
+                    ad += fabsf(fi - fa);
+                    const float dv = fi - m0;
+                    sd1.add(dv);
+                    sdd1.add_prod(dv, dv);
+                    sdy1.add_prod(dv, elem(yc4, j));
+                }
+            }
+        });
+        const bool nc = __any_sync(kFull, ad != 0.0f);
+#pragma unroll
+        for (int o = 16; o >= 1; o >>= 1) se1 += __shfl_xor_sync(kFull, se1, o);
+        if (nc) {
+            sd1.warp_allreduce();
+            sdd1.warp_allreduce();
+            sdy1.warp_allreduce();
+        } else {
+            sd1 = KahanF();
+            sdd1 = KahanF();
+            sdy1 = KahanF();
+        }
+        // Identical on every lane (the reductions are symmetric), so the branch is uniform.
+        const float chk = se1 + (sd1.s + sd1.c) + (sdd1.s + sdd1.c) + (sdy1.s + sdy1.c);
+        if (isfinite(chk)) {
+            if (lane == 0) {
+                uint32_t w[kNumFields];
+                w[kMean] = __float_as_uint(nc ? m0 : fa);
+                w[kMean64] = 0u;
+                w[kSe2] = __float_as_uint(se1);
+                w[kSe2 + 1] = 0u;
+                put_pair(w + kSd, sd1);
+                put_pair(w + kSdd, sdd1);
+                put_pair(w + kSdy, sdy1);
+                w[kTileFlags] = nc ? TF_NONCONST : 0u;
+#pragma unroll
+                for (int f = 0; f < kNumFields; ++f) *field(f) = w[f];
+            }
+            __syncwarp();
+            return 0;
+        }
+    }
+    T v0[4];
+    vals.get4(0, 0, v0);
+    const T f0 = __shfl_sync(kFull, v0[0], 0);
+    Sum sf;
+    bool nonconst = false;
+    float emax = 0.0f, fmax_ = 0.0f, ymax = 0.0f;
+    vals.for_halves(halves, lane, [&](int h, const T (&v)[4]) {
+        const float4 y4 = row4(yrow, h);
+        const float4 yc4 = row4(ycrow, h);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            if (h * 128 + lane * 4 + j < nval) {
+                const T fi = v[j];
+                sf.add(fi);
+                nonconst |= (fi != f0);
+                if constexpr (sizeof(T) == 4) {
+                    emax = fmaxf(emax, fabsf(fi - elem(y4, j)));
+                    fmax_ = fmaxf(fmax_, fabsf(fi));
+                    ymax = fmaxf(ymax, fabsf(elem(yc4, j)));
+                }
+            }
+        }
+    });
+    nonconst = __any_sync(kFull, nonconst);
+    sf.warp_allreduce();
+    int ke = 0, kd = 0, ky = 0;
+    T se_scale = T(1), sd_scale = T(1), sy_scale = T(1);
+    if constexpr (sizeof(T) == 4) {
+#pragma unroll
+        for (int o = 16; o >= 1; o >>= 1) {
+            emax = fmaxf(emax, __shfl_xor_sync(kFull, emax, o));
+            fmax_ = fmaxf(fmax_, __shfl_xor_sync(kFull, fmax_, o));
+            ymax = fmaxf(ymax, __shfl_xor_sync(kFull, ymax, o));
+        }
+        ke = scale_exponent(emax);
+        kd = scale_exponent(2.0f * fmax_);
+        ky = scale_exponent(ymax);
+        se_scale = pow2f(-ke);
+        sd_scale = pow2f(-kd);
+        sy_scale = pow2f(-ky);
+    }
+    T m;
+    if constexpr (sizeof(T) == 4) m = nonconst ? (sf.s + sf.c) / static_cast<float>(nval) : f0;
+    else m = nonconst ? sf.s / static_cast<double>(nval) : f0;
+    Sum se, sd, sdd, sdy;
+    vals.for_halves(halves, lane, [&](int h, const T (&v)[4]) {
+        const float4 y4 = row4(yrow, h);
+        const float4 yc4 = row4(ycrow, h);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            if (h * 128 + lane * 4 + j < nval) {
+                const T fi = v[j];
+                const T e = (fi - static_cast<T>(elem(y4, j))) * se_scale;
+                se.add_prod(e, e);
+                if (nonconst) {
+                    const T dv = (fi - m) * sd_scale;
+                    sd.add(dv);
+                    sdd.add_prod(dv, dv);
+                    // FP32: the stored fp32 y - ybar; FP64: y - ybar formed in fp64.
+                    const T yc = sizeof(T) == 4 ? static_cast<T>(elem(yc4, j))
+                                                : static_cast<T>(elem(y4, j)) -
+                                                      static_cast<T>(J.ybar);
+                    sdy.add_prod(dv, yc * sy_scale);
+                }
+            }
+        }
+    });
+    se.warp_allreduce();
+    if (nonconst) {
+        sd.warp_allreduce();
+        sdd.warp_allreduce();
+        sdy.warp_allreduce();
+    }
+    if (lane == 0) {
+        uint32_t w[kNumFields];
+        if constexpr (sizeof(T) == 4) {
+            w[kMean] = __float_as_uint(m);
+            w[kMean64] = 0u;
+        } else {
+            const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(m));
+            w[kMean] = static_cast<uint32_t>(b);
+            w[kMean64] = static_cast<uint32_t>(b >> 32);
+        }
+        put_pair(w + kSe2, se);
+        put_pair(w + kSd, sd);
+        put_pair(w + kSdd, sdd);
+        put_pair(w + kSdy, sdy);
+        w[kTileFlags] = (nonconst ? TF_NONCONST : 0u) | (static_cast<uint32_t>(ke) << 8) |
+                        (static_cast<uint32_t>(kd) << 16) | (static_cast<uint32_t>(ky) << 24);
+#pragma unroll
+        for (int f = 0; f < kNumFields; ++f) *field(f) = w[f];
+    }
+    __syncwarp();
+    return 0;
+}
+
+// Threads per CTA the kernel is compiled for (the register budget per thread follows from it).
+// The 4-case FP32 path, its stack in tensor memory, gets 32 warps (64 registers a thread):
+// more resident warps hide more of the dispatch latency (C2 population: 17 consumer warps
+// 2,304 GPoPs, 27 at 72 registers 2,656, 31 at 64 registers 2,738); the 2-case path also
+// fits 32 warps; the 8-case and FP64 paths get 16 warps (128 registers).
+// The deep pass (D = 32) of the 4-case path has 16 consumer warps: 128 tensor-memory columns
+// each fill the 512 columns.
+template <typename T, int K, int D>
+struct KernelThreads {
+    static constexpr int value = sizeof(T) != 4 ? 512 : (K == 4 && D > 16) ? 544 :
+                                 K == 2 ? 1024 : K == 4 ? 1024 : 512;
+};
+
+// Finalize: merge each program's tiles in a fixed order in fp64 (Chan et al.'s pairwise
+// update of centred sums), then MSE and 1 - r^2 (Eq. 1, squared).
+template <bool FP64>
+__device__ __forceinline__ double word_pair(const uint32_t *w0, const uint32_t *w1) {
+    if constexpr (FP64) {
+        return __longlong_as_double(static_cast<long long>(
+            (static_cast<unsigned long long>(*w1) << 32) | *w0));
+    } else {
+        return static_cast<double>(__uint_as_float(*w0)) +
+               static_cast<double>(__uint_as_float(*w1));
+    }
+}
+
+// One program's MSE and 1 - r^2 from its tile partials (tile: cases per tile; timed_out: the
+// launch's error word was set).
+template <bool FP64>
+__device__ __forceinline__ void finalize_mse_program(const JobDev &J, int64_t p, int tile,
+                                                     bool timed_out) {
+    const int T = J.tiles;
+    const int64_t P = J.P;
+    auto W = [&](int f, int t) { return J.partials + (static_cast<int64_t>(f) * T + t) * P + p; };
+    beagle_fitness r;
+    r.reserved = 0u;
+    const double inf = __longlong_as_double(0x7ff0000000000000ll);
+    uint32_t flags = 0u;
+    if (timed_out) {
+        r.mse = r.one_minus_r2 = __longlong_as_double(0x7ff8000000000000ll);
+        r.flags = BEAGLE_FLAG_TIMEOUT;
+        J.out[p] = r;
+        return;
+    }
+    bool nonconst = false, mdiff = false;
+    double sse = 0.0, sumf = 0.0, m0 = 0.0;
+    for (int t = 0; t < T; ++t) {
+        const uint32_t tf = *W(kTileFlags, t);
+        if (tf & TF_MALFORMED) flags |= BEAGLE_FLAG_MALFORMED;
+        if (tf & TF_INVALID) flags |= BEAGLE_FLAG_INVALID;
+    }
+    if (flags) {
+        r.mse = r.one_minus_r2 = inf;
+        r.flags = flags;
+        J.out[p] = r;
+        return;
+    }
+    for (int t = 0; t < T; ++t) {
+        const double n = static_cast<double>(min(static_cast<int64_t>(tile),
+                                                 J.N - static_cast<int64_t>(t) * tile));
+        const double m = FP64 ? word_pair<true>(W(kMean, t), W(kMean64, t))
+                              : static_cast<double>(__uint_as_float(*W(kMean, t)));
+        const uint32_t tf = *W(kTileFlags, t);
+        const int ke = (tf >> 8) & 0xff, kd = (tf >> 16) & 0xff;
+        sse += ldexp(word_pair<FP64>(W(kSe2, t), W(kSe2 + 1, t)), 2 * ke);
+        sumf += n * m + ldexp(word_pair<FP64>(W(kSd, t), W(kSd + 1, t)), kd);
+        nonconst |= (tf & TF_NONCONST) != 0u;
+        if (t == 0) m0 = m;
+        else mdiff |= (m != m0);
+    }
+    const double N = static_cast<double>(J.N);
+    r.mse = sse / N;
+    if (!nonconst && !mdiff) {
+        r.one_minus_r2 = 1.0;
+        r.flags = BEAGLE_FLAG_DEGENERATE;
+        J.out[p] = r;
+        return;
+    }
+    const double fbar = sumf / N;
+    double sff = 0.0, sfy = 0.0;
+    for (int t = 0; t < T; ++t) {
+        const double n = static_cast<double>(min(static_cast<int64_t>(tile),
+                                                 J.N - static_cast<int64_t>(t) * tile));
+        const double m = FP64 ? word_pair<true>(W(kMean, t), W(kMean64, t))
+                              : static_cast<double>(__uint_as_float(*W(kMean, t)));
+        const uint32_t tf = *W(kTileFlags, t);
+        const int kd = (tf >> 16) & 0xff, ky = (tf >> 24) & 0xff;
+        const double dm = m - fbar;
+        const double sd = ldexp(word_pair<FP64>(W(kSd, t), W(kSd + 1, t)), kd);
+        sff += ldexp(word_pair<FP64>(W(kSdd, t), W(kSdd + 1, t)), 2 * kd) + 2.0 * dm * sd +
+               n * dm * dm;
+        sfy += ldexp(word_pair<FP64>(W(kSdy, t), W(kSdy + 1, t)), kd + ky) + dm * J.tile_sy[t];
+    }
+    if (!(sff > 0.0)) {
+        r.one_minus_r2 = 1.0;
+        r.flags = BEAGLE_FLAG_DEGENERATE;
+    } else {
+        const double rr = sfy / sqrt(sff * J.syy);
+        r.one_minus_r2 = 1.0 - rr * rr;
+        r.flags = 0u;
+    }
+    J.out[p] = r;
+}
+
+
+// Finalize of the paper's fitness functions: per program, the tiles merged in a fixed order in
+// fp64. Correlation: valid-pair count, c1, c2; the outputs' mean over the valid pairs from the
+// tile means and sums, S_ff by Chan et al.'s update, the targets' sums centred on their own
+// mean over the valid pairs; r (Eq. 1 over the valid pairs), then Eq. 2. Eq. 5 family and
+// validation: the integer tile scores summed.
+template <bool FP64>
+__device__ __forceinline__ double fit_value(const uint32_t *w0, const uint32_t *w1) {
+    if constexpr (FP64)
+        return __longlong_as_double(static_cast<long long>(
+            (static_cast<unsigned long long>(*w1) << 32) | *w0));
+    else
+        return static_cast<double>(__uint_as_float(*w0));
+}
+
+template <bool FP64>
+__device__ __forceinline__ void finalize_fit_program(const JobDev &J, int64_t p, bool timed_out) {
+    const int T = J.tiles;
+    const int64_t P = J.P;
+    auto W = [&](int f, int t) { return J.partials + (static_cast<int64_t>(f) * T + t) * P + p; };
+    beagle_fit_result r;
+    r.score = r.asr = r.r2 = r.taxed_score = 0.0;
+    r.c1 = r.c2 = 0;
+    r.flags = 0u;
+    r.reserved = 0u;
+    if (timed_out) {
+        r.score = r.asr = r.r2 = r.taxed_score = __longlong_as_double(0x7ff8000000000000ll);
+        r.flags = BEAGLE_FLAG_TIMEOUT;
+        J.fit[p] = r;
+        return;
+    }
+    bool malformed = false;
+    long long c1 = 0, c2 = 0, n = 0;
+    for (int t = 0; t < T; ++t) {
+        if (*W(kfFlags, t) & TF_MALFORMED) malformed = true;
+        n += *W(kfN, t);
+        c1 += *W(kfC1, t);
+        c2 += *W(kfC2, t);
+    }
+    if (malformed) {
+        r.score = r.asr = r.taxed_score = -__longlong_as_double(0x7ff0000000000000ll);
+        r.flags = BEAGLE_FLAG_MALFORMED;
+        J.fit[p] = r;
+        return;
+    }
+    const double M = static_cast<double>(J.max_score), N = static_cast<double>(J.N);
+    double score;
+    if (J.kind == kFitCorr) {
+        // constancy over the valid pairs, exactly: every tile's extremes equal, and equal
+        // across the tiles that hold valid pairs
+        bool fconst = true, yconst = true, have = false;
+        double f0 = 0.0;
+        float y0 = 0.0f;
+        for (int t = 0; t < T; ++t) {
+            if (*W(kfN, t) == 0u) continue;
+            const double fmn = fit_value<FP64>(W(kfFmin, t), W(kfFmin + 1, t));
+            const double fmx = fit_value<FP64>(W(kfFmax, t), W(kfFmax + 1, t));
+            const float ymn = __uint_as_float(*W(kfYmin, t)), ymx = __uint_as_float(*W(kfYmax, t));
+            if (fmn != fmx) fconst = false;
+            if (ymn != ymx) yconst = false;
+            if (!have) {
+                f0 = fmn;
+                y0 = ymn;
+                have = true;
+            } else {
+                if (fmn != f0) fconst = false;
+                if (ymn != y0) yconst = false;
+            }
+        }
+        double rr = 0.0;
+        bool degenerate = true;
+        if (n > 0 && !fconst && !yconst) {
+            double sumf = 0.0;
+            for (int t = 0; t < T; ++t) {
+                const double nt = static_cast<double>(*W(kfN, t));
+                if (nt == 0.0) continue;
+                const int kd = (*W(kfFlags, t) >> 16) & 0xff;
+                sumf += nt * fit_value<FP64>(W(kfMean, t), W(kfMean + 1, t)) +
+                        ldexp(word_pair<FP64>(W(kfSd, t), W(kfSd + 1, t)), kd);
+            }
+            const double fbar = sumf / static_cast<double>(n);
+            double sff = 0.0, sy = 0.0, syy = 0.0, sfy = 0.0;
+            for (int t = 0; t < T; ++t) {
+                const double nt = static_cast<double>(*W(kfN, t));
+                if (nt == 0.0) continue;
+                const uint32_t tf = *W(kfFlags, t);
+                const int kd = (tf >> 16) & 0xff, ky = (tf >> 24) & 0xff;
+                const double dm = fit_value<FP64>(W(kfMean, t), W(kfMean + 1, t)) - fbar;
+                const double sd = ldexp(word_pair<FP64>(W(kfSd, t), W(kfSd + 1, t)), kd);
+                const double syt = ldexp(word_pair<FP64>(W(kfSy, t), W(kfSy + 1, t)), ky);
+                sff += ldexp(word_pair<FP64>(W(kfSdd, t), W(kfSdd + 1, t)), 2 * kd) +
+                       2.0 * dm * sd + nt * dm * dm;
+                sy += syt;
+                syy += ldexp(word_pair<FP64>(W(kfSyy, t), W(kfSyy + 1, t)), 2 * ky);
+                sfy += ldexp(word_pair<FP64>(W(kfSdy, t), W(kfSdy + 1, t)), kd + ky) + dm * syt;
+            }
+            syy -= sy * sy / static_cast<double>(n);   // centre on the valid pairs' mean
+            if (sff > 0.0 && syy > 0.0) {
+                rr = sfy / sqrt(sff * syy);
+                degenerate = false;
+            }
+        }
+        if (degenerate) r.flags |= BEAGLE_FLAG_DEGENERATE;
+        const double r2 = rr * rr;
+        r.r2 = r2;
+        score = M * r2 * r2 * static_cast<double>(J.N - (c1 + c2)) - M * static_cast<double>(c1 - c2);
+        r.asr = score / (M * N);
+    } else {
+        long long tot = 0;
+        for (int t = 0; t < T; ++t)
+            tot += static_cast<long long>((static_cast<unsigned long long>(*W(kfScore + 1, t)) << 32) |
+                                          *W(kfScore, t));
+        score = static_cast<double>(tot);
+        if (J.kind == kFitValidate) {
+            r.asr = score / N;
+            if (tot == J.N) r.flags |= BEAGLE_FLAG_PERFECT;
+        } else {
+            r.asr = score / (M * N);
+        }
+    }
+    r.score = score;
+    r.c1 = c1;
+    r.c2 = c2;
+    r.taxed_score = score - J.tax * static_cast<double>(J.lens[p]);
+    J.fit[p] = r;
+}
+
+
+}  // namespace beagle

@@ -72,25 +72,27 @@ extern "C" beagle_status beagle_score_static(const uint8_t *programs, const int6
     if (P > (int64_t(1) << 31) - 1) return fail(BEAGLE_ERR_LIMIT, "P >= 2^31");
     const int tile = tile_for(precision, kCasesFp32, 512);
     const int64_t tiles = (ds->N + tile - 1) / tile;
-    // 44 bytes per program and tile after a 256-byte header; compared without forming the
-    // product, which could wrap for huge P.
-    const int64_t per_program = static_cast<int64_t>(kNumFields) * 4 * tiles;
+    // 44 bytes per program and tile plus 4 per program (the list of programs deeper than the
+    // fast pass's stack) after a 512-byte header; compared without forming the product,
+    // which could wrap for huge P.
+    const int64_t per_program = static_cast<int64_t>(kNumFields) * 4 * tiles + 4;
     const int64_t max_programs =
-        (static_cast<int64_t>(BEAGLE_STATIC_SCRATCH_BYTES) - 512) / per_program;
+        (static_cast<int64_t>(BEAGLE_STATIC_SCRATCH_BYTES) - static_cast<int64_t>(kHdrBytes) -
+         512) / per_program;
     if (P > max_programs)
         return fail(BEAGLE_ERR_LIMIT,
                     "static scratch holds at most %lld programs on %lld tiles of %d cases "
-                    "(44 bytes per program and tile, limit %u bytes); got P = %lld",
-                    (long long)max_programs, (long long)tiles, tile,
+                    "(44 bytes per program and tile and 4 per program, limit %u bytes); got "
+                    "P = %lld", (long long)max_programs, (long long)tiles, tile,
                     (unsigned)BEAGLE_STATIC_SCRATCH_BYTES, (long long)P);
     char *base = nullptr;
     beagle_status st = static_scratch_address(dev, &base);
     if (st != BEAGLE_OK) return st;
 
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    // The array keeps the previous call's contents: the counter and error word must start
-    // at zero (the partials are fully written before they are read).
-    cudaError_t e = cudaMemsetAsync(base, 0, 256, s);
+    // The array keeps the previous call's contents: the counters, error word and deep count
+    // must start at zero (the partials and the deep list are written before they are read).
+    cudaError_t e = cudaMemsetAsync(base, 0, kHdrBytes, s);
     if (e != cudaSuccess) return cuda_fail(e, "static scratch: memset");
 
     const int grid = sm_count();
@@ -110,7 +112,10 @@ extern "C" beagle_status beagle_score_static(const uint8_t *programs, const int6
     J.lens = lengths;
     J.consts = consts;
     J.out = fitness_out;
-    J.partials = reinterpret_cast<uint32_t *>(base + 256);
+    const size_t part_bytes = static_cast<size_t>(kNumFields) * 4 * tiles * P;
+    J.partials = reinterpret_cast<uint32_t *>(base + kHdrBytes);
+    J.deep_list = reinterpret_cast<int32_t *>(base + kHdrBytes + round256(part_bytes));
+    J.deep_count = reinterpret_cast<int32_t *>(base + kHdrDeep);
     J.tile_sy = precision == BEAGLE_FP64 ? ds->tile_sy64[tile == 512 ? 0 : 1]
                                          : ds->tile_sy[tile == 512 ? 0 : 1];
     J.order = nullptr;
@@ -125,8 +130,8 @@ extern "C" beagle_status beagle_score_static(const uint8_t *programs, const int6
     J.ybar = ds->ybar;
     J.syy = precision == BEAGLE_FP64 ? ds->syy : ds->syy32;
     prm.total_items = static_cast<int64_t>(J.groups) * tiles;
-    prm.counter = reinterpret_cast<unsigned int *>(base);
-    prm.error = reinterpret_cast<unsigned int *>(base + 128);
+    prm.counter = reinterpret_cast<unsigned int *>(base + kHdrCounter);
+    prm.error = reinterpret_cast<unsigned int *>(base + kHdrError);
     prm.njobs = 1;
     prm.tile = tile;
     prm.group = group;

@@ -13,7 +13,9 @@ config draws inputs X and computes a target y from a fixed or random expression.
 Wire format (one byte per token; must match ``include/beagle.h``):
 
     0 CONST   1 ADD   2 SUB   3 MUL   4 PDIV   5 SIN   6 COS   7 EXP   8 PLOG
-    9 PSQRT  10 SQUARE  11 DUP  12 SWAP  13 DEL   32+k LOAD x_k (k < 16)
+    9 PSQRT  10 SQUARE  11 DUP  12 SWAP  13 DEL  14 POW  15 SIGN  16 CUBE  17 CBRT
+   18 TAN   19 ASIN  20 ACOS  21 ATAN  22 TANH   32+k LOAD x_k (k < 16)
+   64+k COPY @k   80+k PASTE @k (k < 8)
 
 ``consts`` is token-aligned: ``consts[offsets[p] + j]`` is the value of token j of program
 p when that token is CONST (fp32), and 0 otherwise.
@@ -28,14 +30,31 @@ import numpy as np
 CONST, ADD, SUB, MUL, PDIV = 0, 1, 2, 3, 4
 SIN, COS, EXP, PLOG, PSQRT, SQUARE = 5, 6, 7, 8, 9, 10
 DUP, SWAP, DEL = 11, 12, 13
+POW, SIGN, CUBE, CBRT, TAN, ASIN, ACOS, ATAN, TANH = 14, 15, 16, 17, 18, 19, 20, 21, 22
 LOAD0 = 32
+COPY0, PASTE0, N_REGS = 64, 80, 8
 MAX_VARS = 16
 
+# The default operator set of the benchmark workloads, and the rest of Table 3.
 UNARY = (SIN, COS, EXP, PLOG, PSQRT, SQUARE)
 BINARY = (ADD, SUB, MUL, PDIV)
+UNARY_EXT = (SIGN, CUBE, CBRT, TAN, ASIN, ACOS, ATAN, TANH)
+ALL_UNARY = UNARY + UNARY_EXT
+ALL_BINARY = BINARY + (POW,)
 NAMES = {CONST: "CONST", ADD: "ADD", SUB: "SUB", MUL: "MUL", PDIV: "PDIV", SIN: "SIN",
          COS: "COS", EXP: "EXP", PLOG: "PLOG", PSQRT: "PSQRT", SQUARE: "SQUARE",
-         DUP: "DUP", SWAP: "SWAP", DEL: "DEL"}
+         DUP: "DUP", SWAP: "SWAP", DEL: "DEL", POW: "POW", SIGN: "SIGN", CUBE: "CUBE",
+         CBRT: "CBRT", TAN: "TAN", ASIN: "ARCSIN", ACOS: "ARCCOS", ATAN: "ARCTAN",
+         TANH: "TANH"}
+
+
+def allowed_operations(exclude=()):
+    """The generator's operator sets without the excluded opcodes: the analogue of
+    MLSetup.GetAllowedOperations ("Subclassing MLSetup - optional overrides"), which restricts
+    the operators evolution may use. Returns (unary, binary) for gen_programs."""
+    ex = set(exclude)
+    return (tuple(o for o in ALL_UNARY if o not in ex),
+            tuple(o for o in ALL_BINARY if o not in ex))
 
 # Class weights of the random walk: leaf / unary / binary, renormalised over the classes
 # that can still end in a depth-1 program. The paper gives no distribution; this is ours.
@@ -158,13 +177,38 @@ def gen_programs(seed, P: int, lmin: int, lmax: int, d: int, *,
 
 def stack_effect(op: int) -> tuple[int, int]:
     """(minimum depth before the token, depth change) of one token (Table 3)."""
-    if op == CONST or op >= LOAD0:
+    if op == CONST or LOAD0 <= op < LOAD0 + MAX_VARS:
         return 0, 1
-    if op in BINARY:
+    if COPY0 <= op < COPY0 + N_REGS:
+        return 1, 0
+    if PASTE0 <= op < PASTE0 + N_REGS:
+        return 0, 1
+    if op in ALL_BINARY:
         return 2, -1
-    if op in UNARY:
+    if op in ALL_UNARY:
         return 1, 0
     return {DUP: (1, 1), SWAP: (2, 0), DEL: (1, -1)}[op]
+
+
+def with_registers(progs: "Programs", seed, frac: float = 0.5, n_regs: int = 2) -> "Programs":
+    """Insert COPY @k / PASTE @k pairs (Table 3's variables) into a fraction of the programs:
+    COPY @k after a random token, and later PASTE @k followed by ADD, so that the pasted value
+    is consumed and the program still ends at depth 1. Register k is used at most once per
+    program; registers 0..n_regs-1 are drawn in order."""
+    rng = _rng(seed)
+    out = []
+    for p in range(progs.P):
+        ops, cs = progs.program(p)
+        toks = [(int(o), float(c)) for o, c in zip(ops, cs)]
+        if rng.random() < frac and len(toks) >= 2:
+            for k in range(int(rng.integers(1, n_regs + 1))):
+                n = len(toks)
+                i = int(rng.integers(0, n - 1))          # COPY after token i
+                j = int(rng.integers(i + 1, n))          # PASTE, ADD after token j (j > i)
+                toks = (toks[:i + 1] + [(COPY0 + k, 0.0)] + toks[i + 1:j + 1] +
+                        [(PASTE0 + k, 0.0), (ADD, 0.0)] + toks[j + 1:])
+        out.append(toks)
+    return from_token_lists(out)
 
 
 def max_depth(ops) -> int:

@@ -177,11 +177,13 @@ def test_malformed_programs_are_flagged():
         [(S.ADD, 0)],                                   # underflow
         [(C, 1.0), (C, 2.0)],                           # two values left
         [(L0 + 3, 0)],                                  # x3 with d = 2
-        [(20, 0)],                                      # unknown opcode
-        [(C, 1.0)] * 17 + [(S.ADD, 0)] * 16,            # 17 values > BEAGLE_MAX_DEPTH
+        [(99, 0)],                                      # unknown opcode
+        [(C, 1.0)] * 33 + [(S.ADD, 0)] * 32,            # 33 values > BEAGLE_MAX_DEPTH
         [(C, 1.0)] + [(S.SIN, 0)] * 256,                # 257 tokens > BEAGLE_MAX_LENGTH
+        [(L0, 0), (S.COPY0, 0)] + [(C, 1.0)] * 31 + [(S.ADD, 0)] * 31 +
+        [(S.PASTE0, 0), (S.ADD, 0)],                    # 32 values + a live variable
     ]
-    ok_deep = [(C, 1.0)] * 16 + [(S.ADD, 0)] * 15       # exactly 16 deep
+    ok_deep = [(C, 1.0)] * 32 + [(S.ADD, 0)] * 31       # exactly 32 deep (the deep pass)
     ok_long = [(L0, 0)] + [(S.SIN, 0)] * 255            # exactly 256 tokens
     progs = S.from_token_lists([good] + bad + [ok_deep, ok_long])
     X = np.random.default_rng(0).uniform(-1, 1, size=(2, 300)).astype(np.float32)
@@ -195,6 +197,66 @@ def test_malformed_programs_are_flagged():
     okp = S.from_token_lists([good, ok_deep, ok_long])
     g32 = run_gpu(okp, X, y, "fp32c")
     parity.check_fp32(g32, parity.references(okp, X, y))
+
+
+def _deep_population(rng, P, d):
+    """Programs of every depth up to the paper's StackSize of 32, shallow and deep mixed (and
+    some with COPY/PASTE variables)."""
+    progs = S.gen_programs(rng, P, 30, 200, d, depth_cap=32, weights=(0.55, 0.1, 0.35),
+                           unary=S.ALL_UNARY, binary=S.ALL_BINARY)
+    depth = np.array([S.max_depth(progs.program(p)[0]) for p in range(progs.P)])
+    return progs, depth
+
+
+@pytest.mark.parametrize("cases", [4, 2, 8])
+def test_deep_programs_up_to_stack_size_32(cases):
+    """Programs deeper than the fast pass's 16-value stack run in the deep pass (32 values):
+    parity with the oracle at several tile counts, mixed with shallow programs."""
+    rng = np.random.default_rng(40 + cases)
+    d, N = 3, 1300
+    X = rng.uniform(-1.5, 1.5, (d, N)).astype(np.float32)
+    y = (X[0] * X[1] - np.tanh(X[2])).astype(np.float32)
+    progs, depth = _deep_population(rng, 500, d)
+    assert (depth > 16).sum() >= 100 and (depth <= 16).sum() >= 50 and depth.max() <= 32
+    refs = parity.references(progs, X, y)
+    beagle.set_launch_config(cases_per_lane=cases)
+    try:
+        g32 = run_gpu(progs, X, y, "fp32c")
+        assert not np.any(g32[2] & beagle.FLAG_MALFORMED)
+        parity.check_fp32(g32, refs, name=f"deep-{cases}")
+        if cases == 4:
+            g64 = run_gpu(progs, X, y, "fp64")
+            parity.check_fp64(g64, refs, name="deep")
+    finally:
+        beagle.reset_launch_config()
+
+
+def test_deep_programs_same_bits_alone_in_batch_and_static():
+    rng = np.random.default_rng(44)
+    d, N = 2, 900
+    X = rng.uniform(-1, 1, (d, N)).astype(np.float32)
+    y = (X[0] - X[1] ** 2).astype(np.float32)
+    progs, depth = _deep_population(rng, 300, d)
+    ds = beagle.Dataset(X, y)
+    dp = beagle.DevicePrograms(progs)
+    alone = beagle.unpack_fitness(beagle.score_programs(dp, ds))
+    out = torch.empty((dp.P, 3), dtype=torch.float64, device="cuda")
+    other = S.gen_programs(rng, 700, 4, 60, d)
+    dpo = beagle.DevicePrograms(other)
+    outo = torch.empty((dpo.P, 3), dtype=torch.float64, device="cuda")
+    beagle.score_batch([(dpo, ds, outo), (dp, ds, out)])
+    torch.cuda.synchronize()
+    for a, b in zip(beagle.unpack_fitness(out), alone):
+        assert np.array_equal(a, b, equal_nan=True)
+    st = torch.empty((dp.P, 3), dtype=torch.float64, device="cuda")
+    beagle.check(beagle.lib().beagle_score_static(
+        dp.ops.data_ptr(), dp.offsets.data_ptr(), dp.lengths.data_ptr(), dp.consts.data_ptr(),
+        dp.P, ds.id, st.data_ptr(), beagle.FP32_COMPENSATED,
+        torch.cuda.current_stream().cuda_stream))
+    torch.cuda.synchronize()
+    for a, b in zip(beagle.unpack_fitness(st), alone):
+        assert np.array_equal(a, b, equal_nan=True)
+    ds.release()
 
 
 def test_invalid_values_and_constants():
