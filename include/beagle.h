@@ -1,23 +1,25 @@
 /*
  * beagle.h -- C ABI of the GB300 population-scoring library (libbeagle.so).
  *
- * What the library computes follows the Beagle tutorial (arXiv 2607.06731):
- *   - A genome is a GCL program in reverse Polish notation run on a value stack
- *     (Section 3.2 and Table 3). Unary ops replace the top value; binary ops pop the top b
- *     and the value below it a and push a (op) b (SUB is a - b, DIV is a / b).
+ * What the library computes follows the Beagle tutorial (arXiv 2607.06731), cited by section
+ * title:
+ *   - A genome is a GCL program in reverse Polish notation run on a value stack (the GCL
+ *     section and Table 3). Unary ops replace the top value; binary ops pop the top b and the
+ *     value below it a and push a (op) b (SUB is a - b, DIV is a / b, POW is a ^ b).
  *   - The GPU evaluates each program on every fitness case and returns one aggregated
- *     fitness per program; the CPU keeps the genetic operators (Section 2.4). Genomes go to
- *     the device once per generation and datasets stay resident (Sections 2.4, 3.6).
- *   - Fitness is the mean squared error and 1 - r^2, r being the Pearson correlation of
- *     Eq. 1 between outputs and targets, squared (Section 2.10).
+ *     fitness per program; the CPU keeps the genetic operators ("Dividing Tasks Between CPU
+ *     and GPU"). Genomes go to the device once per generation and datasets stay resident.
+ *   - Fitness: the mean squared error and 1 - r^2, r being the Pearson correlation of Eq. 1
+ *     between outputs and targets, squared ("Fitness Functions"); and the paper's own fitness
+ *     functions, Eqs. 2 and 5 (beagle_score_fit).
  *
  * Readings of points the paper leaves open (the paper's own DIV, LN, SQRT are unprotected):
  *   pdiv(a, b) = a / b if |b| > 1e-3, else 1;  plog(a) = ln|a| if |a| > 1e-3, else 0;
- *   psqrt(a) = sqrt|a|.  A program is INVALID when any value it produces is non-finite or
- *   has |v| > 1e30; an invalid program scores +inf for both fitness values. When a program's
- *   output is the same on every case, r is undefined and 1 - r^2 is reported as 1
- *   (flag DEGENERATE). Thresholds are compared in the arithmetic's own precision (the fp32
- *   value nearest 1e30 and 1e-3 on the FP32 path).
+ *   psqrt(a) = sqrt|a|; the rest of Table 3 is unprotected. A program is INVALID when any
+ *   value it produces is non-finite or has |v| > 1e30; an invalid program scores +inf for
+ *   both fitness values. When a program's output is the same on every case, r is undefined
+ *   and 1 - r^2 is reported as 1 (flag DEGENERATE). Thresholds are compared in the
+ *   arithmetic's own precision (the fp32 value nearest 1e30 and 1e-3 on the FP32 path).
  *
  * Conventions for every call:
  *   - Return value: BEAGLE_OK (0) or a negative BEAGLE_ERR_* code; beagle_last_error()
@@ -106,7 +108,7 @@ typedef int32_t beagle_status;
 #define BEAGLE_FP32_COMPENSATED 0   /* fp32 ops; fp32 compensated sums; fp64 cross-tile merge */
 #define BEAGLE_FP64             1   /* every op and sum in fp64 (plain sums) */
 
-/* One aggregated fitness per program (Section 2.4), 24 bytes. */
+/* One aggregated fitness per program ("Dividing Tasks Between CPU and GPU"), 24 bytes. */
 typedef struct beagle_fitness {
     double mse;           /* (1/N) sum_i (f(x_i) - y_i)^2 */
     double one_minus_r2;  /* 1 - r^2, r from Eq. 1 */
@@ -115,8 +117,9 @@ typedef struct beagle_fitness {
 } beagle_fitness;
 
 /*
- * Upload a dataset and keep it resident on the current device (Section 2.4: data is sent
- * once; Section 3.6: one (inputs, output) point per fitness case).
+ * Upload a dataset and keep it resident on the current device ("Dividing Tasks Between CPU
+ * and GPU": data is sent once; the MLSetup mandatory overrides: one (inputs, output) point
+ * per fitness case).
  *   X      [d][N] fp32, row k holds input x_k of every case (column-major by case).
  *   y      [N] fp32 targets.
  *   N >= 2, 1 <= d <= BEAGLE_MAX_VARS. inputs_on_device: 0 = host pointers, 1 = device.
@@ -175,8 +178,8 @@ beagle_status beagle_validate_programs_ex(const uint8_t *programs, const int64_t
                                           int32_t n_allowed, int64_t *first_bad);
 
 /*
- * Score a population against a resident dataset (Section 2.4). All array pointers are
- * device pointers:
+ * Score a population against a resident dataset ("Dividing Tasks Between CPU and GPU"). All
+ * array pointers are device pointers:
  *   programs  concatenated tokens; program p is programs[offsets[p] .. offsets[p]+lengths[p])
  *   offsets   [P] int64, lengths [P] int32
  *   consts    token-aligned fp32: consts[offsets[p] + j] is read when token j is CONST
@@ -259,7 +262,7 @@ beagle_status beagle_score_fit(const uint8_t *programs, const int64_t *offsets,
 
 /*
  * Run each program on every case and keep the outputs (the paper's ExecuteGenome utility,
- * Section 3.8): same arguments and results as beagle_score, plus outputs, a device array of
+ * "Useful Utilities"): same arguments and results as beagle_score, plus outputs, a device array of
  * P x N values (row p holds program p's output on every case), fp32 for
  * BEAGLE_FP32_COMPENSATED and fp64 for BEAGLE_FP64. Outputs of malformed programs are not
  * written. Asynchronous on stream.
@@ -414,8 +417,9 @@ beagle_status beagle_kernel_timing(int32_t enable);
 beagle_status beagle_kernel_time(double *total_ms, int64_t *launches);
 
 /*
- * Ragged batches (the paper batches populations to fit device memory, Section 2.2; here many
- * (population, dataset) pairs share one persistent launch). A job is one beagle_score call's
+ * Ragged batches (the paper batches populations to fit device memory, "Hardware Optimized";
+ * here many (population, dataset) pairs share one persistent launch). A job is one
+ * beagle_score call's
  * arguments (device pointers, as for beagle_score). Jobs may use different datasets, sizes
  * and program lengths; programs are processed in a length-bucketed order (longest first).
  * Results are the same bits as scoring each job alone.

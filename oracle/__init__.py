@@ -5,7 +5,7 @@ by the benchmark's CPU-baseline leg, and by nothing on the product path. It shar
 with the CUDA path; see ``oracle.c`` for what it computes and which passages it follows.
 
 Pins (tests/test_oracle_*.py): the paper's two worked genomes against the closed-form
-quadratic root (Section 3.3); per-opcode values by hand (Table 3); closed-form MSE;
+quadratic root ("Understanding Beagle Output"); per-opcode values by hand (Table 3); closed-form MSE;
 1 - r^2 against numpy's correlation and a least-squares fit; invariance under permuting
 cases; brute force over every program up to length 5 on a tiny alphabet against an exact
 rational evaluator built on a different algorithm (tree reconstruction).

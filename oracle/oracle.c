@@ -7,13 +7,13 @@
  *
  * What it computes (Beagle tutorial, arXiv 2607.06731):
  *   - Genomes are GCL programs in reverse Polish notation run on a value stack
- *     (Section 3.2, Table 3). Unary ops replace the top; binary ops pop the top b and the
+ *     (the GCL section, Table 3). Unary ops replace the top; binary ops pop the top b and the
  *     element below it a, and push a (op) b: SUB is a - b, DIV is a / b (Table 3).
- *   - The stack holds at most 32 values (StackSize, Section 3.2).
+ *   - The stack holds at most 32 values (StackSize, the GCL section).
  *   - Each program runs on every fitness case and one aggregated fitness per program is
- *     returned (Section 2.4).
+ *     returned ("Dividing Tasks Between CPU and GPU").
  *   - Fitness: mean squared error, and 1 - r^2 with r the Pearson correlation of Eq. 1
- *     (Section 2.10: the paper squares r).
+ *     ("Fitness Functions": the paper squares r).
  * Readings where the paper is silent (protected operators, the validity rule, the
  * degenerate-r rule) are stated where they are used below.
  *
@@ -59,7 +59,7 @@ enum { ORACLE_FP64 = 0, ORACLE_FP32 = 1 };
 #define OF_NEAR     256u    /* diagnostic: a value came within 1e-5 (relative) of a threshold */
 #define OF_AMBIG    512u    /* error bound: a threshold or validity decision lies inside it */
 
-#define ORACLE_STACK 32     /* StackSize (Section 3.2) */
+#define ORACLE_STACK 32     /* StackSize (the GCL section) */
 
 /* Error codes of the check function. */
 #define OE_OK 0
@@ -248,7 +248,7 @@ uint32_t oracle_eval(const uint8_t *ops, const float *cs, int32_t L, const float
 }
 
 /*
- * Aggregate outputs f against targets y (Section 2.10).
+ * Aggregate outputs f against targets y ("Fitness Functions").
  *   mse          = (1/N) sum (f_i - y_i)^2
  *   one_minus_r2 = 1 - r^2, r from Eq. 1 with means over all N cases.
  * Reading: when every f_i is the same value, r is undefined; 1 - r^2 := 1 and

@@ -19,7 +19,7 @@ namespace beagle {
 #define BG_PTX_TRACK4                                                                      \
     BG_PTX_TRACK("%0", "%4") BG_PTX_TRACK("%1", "%5") BG_PTX_TRACK("%2", "%6")             \
     BG_PTX_TRACK("%3", "%7")
-// dst = |den| > 1e-3 ? num / den : 1   (protected division, Section 2.10 reading). The
+// dst = |den| > 1e-3 ? num / den : 1   (protected division, "Fitness Functions" reading). The
 // quotient is rounded to nearest by Markstein's method, without branches: y = rcp.approx(den)
 // refined by one Newton step to the correctly rounded 1/den, w = num y, then w + (num - den w) y
 // with the remainder exact by FMA (the same steps as Arith<float>::pdiv).

@@ -183,10 +183,10 @@ beagle_status score_jobs(const JobRequest *reqs, int n, int precision, cudaStrea
     }
     if (jobs.empty()) return BEAGLE_OK;
 
-    // Launches: jobs in ascending order of input rows (d + 2), cut where the rows change once
-    // the launch holds enough work to fill the GPU, and at kMaxJobs jobs. A launch's shared
-    // memory is sized by its widest dataset, so mixing a narrow dataset into a wide launch
-    // would cost it consumer warps; tiny jobs still share launches.
+    // Launches: jobs in ascending order of input rows (d + 2), up to kMaxJobs jobs each. A
+    // launch's shared memory is sized by its widest dataset; where that would cost the launch
+    // consumer warps (the shared-memory-stack paths) and it already holds enough work to fill
+    // the GPU, the launch is cut where the rows change.
     std::vector<size_t> idx(jobs.size());
     for (size_t i = 0; i < idx.size(); ++i) idx[i] = i;
     std::stable_sort(idx.begin(), idx.end(),
@@ -237,7 +237,7 @@ beagle_status score_jobs(const JobRequest *reqs, int n, int precision, cudaStrea
             JobDev &J = lj[i].dev;
             J.tiles = static_cast<int32_t>((J.N + tile - 1) / tile);
             J.tile_sy = precision == BEAGLE_FP64 ? lds[i]->tile_sy64[which] : lds[i]->tile_sy[which];
-            lj[i].part_bytes = static_cast<size_t>(J.kind == kFitMse ? kNumFields : kNumFitFields) *
+            lj[i].part_bytes = static_cast<size_t>(J.kind == kFitMse ? static_cast<int>(kNumFields) : static_cast<int>(kNumFitFields)) *
                                J.tiles * J.P * sizeof(uint32_t);
             work += J.P * J.tiles;
         }
@@ -250,10 +250,20 @@ beagle_status score_jobs(const JobRequest *reqs, int n, int precision, cudaStrea
         return enqueue<kMaxJobs>(lj, 0, lj.size(), precision, cases, tile, group, nw, grid,
                                  xbuf_floats, sort, s);
     };
+    // Consumer warps a launch would get with stage buffers for `rows` input rows (the shape a
+    // launch takes without an autotuned entry): a wider dataset costs warps only on the paths
+    // whose stacks live in shared memory; on the default path 31 warps fit up to d = 16.
+    auto warps_for = [&](int rows) {
+        const int cases = cfg0.cases ? cfg0.cases : kCasesFp32;
+        const int tile = tile_for(precision, cases, cfg0.tile);
+        int nw = plan_warps(precision, cases, rows * tile, tile);
+        return cfg0.warps ? std::min(nw, cfg0.warps) : nw;
+    };
     for (size_t i : idx) {
         if (!cur.empty() && (cur.size() == static_cast<size_t>(kMaxJobs) ||
                              (jobs[i].dev.rows != jobs[cur.back()].dev.rows &&
-                              cur_cases >= kLaunchCases))) {
+                              cur_cases >= kLaunchCases &&
+                              warps_for(jobs[i].dev.rows) < warps_for(jobs[cur.back()].dev.rows)))) {
             const beagle_status st = flush();
             if (st != BEAGLE_OK) return st;
         }

@@ -4,10 +4,10 @@ This module only draws inputs. It scores nothing: it computes no fitness, applie
 protected operator and checks no intermediate value. The CUDA path and the oracle both
 consume what it returns and share nothing else.
 
-Programs are Beagle GCL genomes (Section 3.2, Table 3): postfix token lists run on a value
-stack. The paper draws new genomes by mutation on the CPU (Section 2.4); this generator
+Programs are Beagle GCL genomes (the GCL section, Table 3): postfix token lists run on a value
+stack. The paper draws new genomes by mutation on the CPU ("Dividing Tasks Between CPU and GPU"); this generator
 stands in for that host side with a plain random walk over valid programs. Datasets stand
-in for a user's ``MLSetup.GetNextInputsAndCorrectOutput`` data source (Section 3.6): each
+in for a user's ``MLSetup.GetNextInputsAndCorrectOutput`` data source (the MLSetup mandatory overrides): each
 config draws inputs X and computes a target y from a fixed or random expression.
 
 Wire format (one byte per token; must match ``include/beagle.h``):

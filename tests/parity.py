@@ -30,7 +30,49 @@ TOL64 = (1e-12, 1e-13)
 # Floors of the strict (well-conditioned) fraction per named check: a regression that pushes
 # programs out of the strict set (a looser bound, a wrong flag) fails the floor even when
 # every remaining strict program passes. Set a little below the fractions measured on a GB300.
-STRICT_FLOORS: dict[str, float] = {}
+# The strict set depends on the oracle alone (its bounds, its two modes), so for fixed seeded
+# inputs the fraction is fixed; the floors sit 5 % below the measured values to absorb
+# libm differences between host architectures.
+STRICT_FLOORS: dict[str, float] = {
+    "batch-0/fp32": 0.052,
+    "batch-1/fp32": 0.146,
+    "batch-2/fp32": 0.066,
+    "batch-3/fp32": 0.097,
+    "batch-4/fp32": 0.097,
+    "batch-5/fp32": 0.071,
+    "c1/fp32": 0.329,
+    "c1/fp64": 0.817,
+    "c2-3000/fp32": 0.059,
+    "c2-3000/fp64": 0.448,
+    "c2-full-1500/fp32": 0.058,
+    "c3-500/fp32": 0.393,
+    "c3-500/fp64": 0.720,
+    "ops-1500/fp64": 0.212,
+    "ops-2-1500/fp32": 0.115,
+    "ops-2-700/fp32": 0.123,
+    "ops-4-1500/fp32": 0.107,
+    "ops-4-700/fp32": 0.131,
+    "ops-700/fp64": 0.253,
+    "ops-8-1500/fp32": 0.145,
+    "ops-8-700/fp32": 0.129,
+    "serve-0/fp32": 0.661,
+    "serve-1/fp32": 0.320,
+    "tiles-1024-12/fp32": 0.226,
+    "tiles-1024-12/fp64": 0.619,
+    "tiles-1025-3/fp32": 0.220,
+    "tiles-1025-3/fp64": 0.682,
+    "tiles-2-1/fp32": 0.066,
+    "tiles-2-1/fp64": 0.053,
+    "tiles-2500-10/fp32": 0.201,
+    "tiles-2500-10/fp64": 0.617,
+    "tiles-3000-13/fp32": 0.210,
+    "tiles-3000-13/fp64": 0.647,
+    "tiles-4096-5/fp32": 0.199,
+    "tiles-4096-5/fp64": 0.594,
+    "tiles-700-16/fp32": 0.227,
+    "tiles-700-16/fp64": 0.646,
+
+}
 
 
 def _report(name, kind, frac):

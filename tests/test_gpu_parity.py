@@ -107,7 +107,7 @@ def _quadratic(n=1024, seed=3):
 
 
 def test_paper_genomes_on_gpu():
-    """Section 3.3's genomes (DUP, DEL, DIV by self, SQUARE) solve the quadratic."""
+    """"Understanding Beagle Output"'s genomes (DUP, DEL, DIV by self, SQUARE) solve the quadratic."""
     X, y = _quadratic()
     progs = S.from_token_lists([t for _, t in paper_genomes().values()])
     refs = parity.references(progs, X, y)

@@ -159,7 +159,7 @@ def _quadratic_data(n=512, seed=7):
 
 @pytest.mark.parametrize("name", ["genome1", "genome2"])
 def test_paper_genomes_solve_the_quadratic(name):
-    """Section 3.3: both printed genomes reach ASR 1.0 on QuadraticEq, i.e. they compute
+    """"Understanding Beagle Output": both printed genomes reach ASR 1.0 on QuadraticEq, i.e. they compute
     the root (-b + sqrt(b^2 - 4ac)) / (2a). Checked against that closed form."""
     n, toks = paper_genomes()[name]
     assert len(toks) == n
