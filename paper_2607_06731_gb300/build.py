@@ -17,7 +17,7 @@ CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libbeagle.so")
 SOURCES = ["api.cu", "plan.cu", "score_kernels.cu", "serve_kernels.cu", "measure.cu", "static_scratch.cu",
-           "order.cu", "batch.cu", "serve.cu", "rank.cu", "shard.cu"]
+           "order.cu", "batch.cu", "serve.cu", "rank.cu", "shard.cu", "pack.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I", os.path.join(ROOT, "include"), "-Xptxas", "-v"]

@@ -90,7 +90,21 @@ struct JobDev {
     int32_t max_score;       // M of the paper's fitness functions
     double tax;              // length tax per token
     beagle_fit_result *fit;  // [P] results of the paper's fitness functions
+    // Programs packed once per call by the packing kernel (or null: each work item packs its
+    // program itself): position q of the order holds its tokens at packed + poff[q] and its
+    // packer result in pmeta[q] (kPackNone where it was not packed).
+    uint2 *packed;
+    const uint32_t *poff;
+    uint32_t *pmeta;
 };
+
+// Packer result of a pre-packed program: bits 0-15 the handler count, then the flags.
+constexpr uint32_t kPackMalformed = 1u << 16;
+constexpr uint32_t kPackDeep = 1u << 17;
+constexpr uint32_t kPackConstBad = 1u << 18;
+constexpr uint32_t kPackNone = 0xffffffffu;   // not packed (no room): the work item packs it
+// Room in the packed-token buffer: this many tokens (8 bytes each) per program on average.
+constexpr int64_t kPackedPerProgram = 136;
 
 template <int MAXJ>
 struct LaunchParams {

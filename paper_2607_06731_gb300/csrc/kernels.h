@@ -18,15 +18,18 @@ inline int plan_group(int64_t work, int nw, int grid) {
     return static_cast<int>(g < lo ? lo : (g > 256 ? 256 : g));
 }
 
-// Cases per tile for a launch shape: the 8-case FP32 path runs one 256-case tile per pass;
-// the others default to 512.
-inline int tile_for(int precision, int cases, int requested) {
-    if (precision == BEAGLE_FP32_COMPENSATED && cases == 8) return 256;
+// Cases per tile for a launch shape: 512 unless the caller asks for 256.
+inline int tile_for(int /*precision*/, int /*cases*/, int requested) {
     return requested ? requested : 512;
 }
 constexpr int kCasesFp64 = 2;              // fitness cases per lane per pass, FP64 path
 // Dynamic shared memory per CTA: 227 KB less room for the kernel's static work table.
 constexpr size_t kSmemBudget = 225 * 1024;
+// The persistent kernels take their SM's tensor memory whole, so they request at least this
+// much shared memory: two CTAs of them never share an SM (the second's allocation would wait
+// for the first to finish, and the SM it left idle would stay idle).
+constexpr size_t kOneCtaPerSmSmem = 116 * 1024;
+inline size_t one_cta_per_sm(size_t smem) { return smem > kOneCtaPerSmSmem ? smem : kOneCtaPerSmSmem; }
 
 // Dynamic shared memory of one CTA with nw consumer warps and `cases` cases per lane.
 size_t smem_bytes(int precision, int cases, int xbuf_floats, int tile, int nw);
@@ -39,13 +42,22 @@ int plan_warps(int precision, int cases, int xbuf_floats, int tile);
 cudaError_t launch_score(const LaunchParams<1> &prm, int precision, int cases, int nw, int grid,
                          cudaStream_t s);
 // Length-bucketed order of each job's programs (longest first), written to order[j].
+// Where poff[j] is set, the same kernel gives each position of the order its offset in a
+// packed-token buffer of pcap[j] tokens (each program its length + 1 tokens, in order; those
+// that do not fit, and lengths outside [1, kMaxLen], get kPackNone).
 struct OrderParams {
     const int32_t *lens[kMaxJobs];
     int32_t *order[kMaxJobs];
+    uint32_t *poff[kMaxJobs];
+    int64_t pcap[kMaxJobs];
     int64_t P[kMaxJobs];
     int32_t njobs;
 };
 cudaError_t launch_length_order(const OrderParams &prm, cudaStream_t s);
+// Pack every program of the jobs that carry a packed-token buffer (JobDev::packed), once per
+// call, for the fast pass's 16-value stack; programs deeper than that go to the deep lists.
+template <int MAXJ>
+cudaError_t launch_pack(const LaunchParams<MAXJ> &prm, int precision, cudaStream_t s);
 
 // Opt-in CUDA-event timing of scoring-kernel launches (beagle_kernel_timing).
 bool timing_enabled();

@@ -72,9 +72,17 @@ beagle_status enqueue(const std::vector<Planned> &jobs, size_t b, size_t e, int 
     // header (work counters, error word, deep counts), then per job: partials, the
     // length order (when sorting) and the list of programs deeper than the fast pass's stack
     size_t scratch = kHdrBytes;
+    // (when sorting, also the packed-token buffer, its offsets and the packer results)
+    auto pack_cap = [](int64_t P) {
+        const int64_t c = P * kPackedPerProgram;
+        return c < int64_t(0xfffffffe) ? c : int64_t(0xfffffffe);
+    };
     for (size_t i = b; i < e; ++i) {
         scratch += up256(jobs[i].part_bytes) + up256(sizeof(int32_t) * jobs[i].dev.P);
-        if (sort && !jobs[i].dev.order) scratch += up256(sizeof(int32_t) * jobs[i].dev.P);
+        if (sort && !jobs[i].dev.order)
+            scratch += up256(sizeof(int32_t) * jobs[i].dev.P) +
+                       up256(sizeof(uint2) * pack_cap(jobs[i].dev.P)) +
+                       2 * up256(sizeof(uint32_t) * jobs[i].dev.P);
     }
     char *base = nullptr;
     cudaError_t err = cudaMallocAsync(reinterpret_cast<void **>(&base), scratch, s);
@@ -104,8 +112,19 @@ beagle_status enqueue(const std::vector<Planned> &jobs, size_t b, size_t e, int 
             int32_t *ord = reinterpret_cast<int32_t *>(cur);
             cur += up256(sizeof(int32_t) * jobs[i].dev.P);
             prm.jobs[nj].order = ord;
+            uint2 *packed = reinterpret_cast<uint2 *>(cur);
+            cur += up256(sizeof(uint2) * pack_cap(jobs[i].dev.P));
+            uint32_t *poff = reinterpret_cast<uint32_t *>(cur);
+            cur += up256(sizeof(uint32_t) * jobs[i].dev.P);
+            uint32_t *pmeta = reinterpret_cast<uint32_t *>(cur);
+            cur += up256(sizeof(uint32_t) * jobs[i].dev.P);
+            prm.jobs[nj].packed = packed;
+            prm.jobs[nj].poff = poff;
+            prm.jobs[nj].pmeta = pmeta;
             op.lens[op.njobs] = jobs[i].dev.lens;
             op.order[op.njobs] = ord;
+            op.poff[op.njobs] = poff;
+            op.pcap[op.njobs] = pack_cap(jobs[i].dev.P);
             op.P[op.njobs] = jobs[i].dev.P;
             ++op.njobs;
         }
@@ -120,6 +139,7 @@ beagle_status enqueue(const std::vector<Planned> &jobs, size_t b, size_t e, int 
     prm.xbuf_floats = xbuf_floats;
     apply_wait_settings(&prm.wait_limit_ns, &prm.stall_producer);
     cudaError_t le = launch_length_order(op, s);
+    if (le == cudaSuccess) le = launch_pack(prm, precision, s);
     if (le == cudaSuccess) {
         if constexpr (MAXJ == 1) le = launch_score(prm, precision, cases, nw, grid, s);
         else le = launch_score_batch(prm, precision, cases, nw, grid, s);

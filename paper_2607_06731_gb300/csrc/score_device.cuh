@@ -14,9 +14,10 @@ namespace beagle {
 //   [0, 64)        mbarriers: full[2], empty[2]
 //   [64, 128)      slot descriptors (2 x Slot)
 //   [128, ...)     X stage buffers: 2 x xbuf_floats fp32 (TMA destinations, 128-byte aligned)
-//   ...            per-warp output buffers: nw x tile x T (none on the 8-case FP32 path)
+//   ...            per-warp output buffers: nw x tile x T
 //   ...            per-warp packed programs: nw x (kMaxLen + 2) x uint2
-//   ...            per-warp value stacks: nw x (kMaxDepth - 1) rows x 32 K x T
+//   ...            per-warp value stacks: nw x (D - 1) rows x 32 K x T (none where the
+//                  stack lives in tensor memory)
 struct Slot {
     int job;        // -1: no more work
     int tile;
@@ -43,18 +44,22 @@ __device__ __forceinline__ void tmem_fence_after_sync() {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 }
 
-// The 4-case FP32 path keeps its stack rows in tensor memory (64 columns a warp, the warp's
-// 32-lane quarter of TMEM being warp % 4 and its column slot warp / 4); the other paths keep
-// them in shared memory.
+// The 4- and 8-case FP32 paths keep their stack rows in tensor memory (the warp's 32-lane
+// quarter of TMEM being warp % 4 and its column slot warp / 4); the other paths keep them in
+// shared memory.
 template <typename T, int K>
-constexpr bool kTmemStackPath = sizeof(T) == 4 && K == 4;
-// Columns a warp's stack takes: D - 1 rows of 4 columns, rounded to a power of two (64 for
-// the 16-value fast pass, 128 for the 32-value deep pass: 16 warps fill the 512 columns).
-__host__ __device__ constexpr int tmem_cols_per_warp(int D) { return D <= 16 ? 64 : 128; }
-static_assert(4 * (kDepthFast - 1) <= tmem_cols_per_warp(kDepthFast), "rows fit the columns");
-static_assert(4 * (kMaxDepth - 1) <= tmem_cols_per_warp(kMaxDepth), "rows fit the columns");
-__host__ __device__ constexpr uint32_t tmem_columns(int nw, int D) {   // power of two, 32..512
-    const int need = (nw + 3) / 4 * tmem_cols_per_warp(D);
+constexpr bool kTmemStackPath = sizeof(T) == 4 && (K == 4 || K == 8);
+// Columns a warp's stack takes: D - 1 rows of K columns, rounded to a power of two (4 cases:
+// 64 for the 16-value fast pass, 128 for the 32-value deep pass; 8 cases: 128 for the fast
+// pass, so 16 warps fill the 512 columns).
+__host__ __device__ constexpr int tmem_cols_per_warp(int D, int K) {
+    return K * (D - 1) <= 64 ? 64 : K * (D - 1) <= 128 ? 128 : 256;
+}
+static_assert(4 * (kDepthFast - 1) <= tmem_cols_per_warp(kDepthFast, 4), "rows fit the columns");
+static_assert(4 * (kMaxDepth - 1) <= tmem_cols_per_warp(kMaxDepth, 4), "rows fit the columns");
+static_assert(8 * (kDepthFast - 1) <= tmem_cols_per_warp(kDepthFast, 8), "rows fit the columns");
+__host__ __device__ constexpr uint32_t tmem_columns(int nw, int D, int K) {   // power of two, 32..512
+    const int need = (nw + 3) / 4 * tmem_cols_per_warp(D, K);
     return need <= 32 ? 32u : need <= 64 ? 64u : need <= 128 ? 128u : need <= 256 ? 256u : 512u;
 }
 
@@ -67,8 +72,7 @@ struct SmemLayout {
         return xbuf_off() + 2ull * xbuf_floats * sizeof(float);
     }
     static __host__ __device__ size_t pbuf_off(int xbuf_floats, int tile, int nw) {
-        return fbuf_off(xbuf_floats) +
-               (sizeof(T) == 4 && K == 8 ? 0 : static_cast<size_t>(nw) * tile * sizeof(T));
+        return fbuf_off(xbuf_floats) + static_cast<size_t>(nw) * tile * sizeof(T);
     }
     static __host__ __device__ size_t stack_off(int xbuf_floats, int tile, int nw) {
         return pbuf_off(xbuf_floats, tile, nw) + static_cast<size_t>(nw) * (kMaxLen + 2) * sizeof(uint2);
@@ -81,24 +85,15 @@ struct SmemLayout {
     }
 };
 
-// The 8-case FP32 path runs one 256-case tile per pass and keeps the outputs in registers;
-// the other paths write them to the warp's shared-memory buffer.
-template <typename T, int K>
-constexpr bool kOutputsInRegs = sizeof(T) == 4 && K == 8;
-
-// A tile's outputs in the order the statistics read them: lane l's values are the cases
-// 128 h + 4 l + j (h over the tile's 128-case halves, j = 0..3), the order in which the 8-case
-// path holds them, so every path forms the same sums in the same order.
+// A tile's outputs, in the warp's shared-memory buffer in case order, read the way the
+// statistics take them: lane l's values are the cases 128 h + 4 l + j (h over the tile's
+// 128-case halves, j = 0..3), so every path forms the same sums in the same order.
 template <typename T, int K>
 struct TileValues {
-    T r[kOutputsInRegs<T, K> ? 8 : 1];
     const T *buf;
-    // values 4h..4h+3 of this lane (h a compile-time index on the register path)
+    // values 4h..4h+3 of this lane
     __device__ __forceinline__ void get4(int h, int lane, T (&v)[4]) const {
-        if constexpr (kOutputsInRegs<T, K>) {
-#pragma unroll
-            for (int j = 0; j < 4; ++j) v[j] = r[4 * h + j];
-        } else if constexpr (sizeof(T) == 4) {
+        if constexpr (sizeof(T) == 4) {
             const float4 q = *reinterpret_cast<const float4 *>(buf + h * 128 + lane * 4);
             v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
         } else {
@@ -110,22 +105,11 @@ struct TileValues {
     // f(h, v) for every 128-case half of the tile that holds cases
     template <typename F>
     __device__ __forceinline__ void for_halves(int halves, int lane, F &&f) const {
-        if constexpr (kOutputsInRegs<T, K>) {
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                if (h < halves) {
-                    T v[4];
-                    get4(h, lane, v);
-                    f(h, v);
-                }
-            }
-        } else {
 #pragma unroll 1
-            for (int h = 0; h < halves; ++h) {
-                T v[4];
-                get4(h, lane, v);
-                f(h, v);
-            }
+        for (int h = 0; h < halves; ++h) {
+            T v[4];
+            get4(h, lane, v);
+            f(h, v);
         }
     }
 };
@@ -356,34 +340,59 @@ __device__ __forceinline__ void fit_tile_stats(const JobDev &J, int nval, bool a
 
 // Score program p on tile t: the partials of (p, t) are written. Returns 1 instead when the
 // program is deeper than this kernel's stack and was left to the deep pass (its partials are
-// not written here), else 0.
-template <typename T, int K, int D>
-__device__ __forceinline__ int process_program(const JobDev &J, int64_t p, int t, int tile,
-                                                const float *xs, uint2 *pbuf, T *fbuf, T *stk,
-                                                uint32_t tstk, int lane) {
+// not written here), else 0. FIT: the job scores with the paper's fitness (J.kind != MSE); a
+// compile-time flag, so the MSE code the hot loop runs carries none of the fitness branches.
+template <typename T, int K, int D, bool FIT>
+__device__ __forceinline__ int process_program_kind(const JobDev &J, int64_t q, int64_t p, int t,
+                                                    int tile, const float *xs, uint2 *pbuf,
+                                                    T *fbuf, T *stk, uint32_t tstk, int lane) {
     using Sum = typename SumOf<T>::type;
-    constexpr bool kRegs = kOutputsInRegs<T, K>;
     constexpr int CH = 32 * K;
-    const int64_t off = J.offs[p];
-    const int L = J.lens[p];
-    const Packed pk = pack_program<T, D>(J.ops + off, J.consts + off, L, J.d, pbuf, lane);
-    if (pk.deep) {
-        // Deeper than this pass's stack: the deep pass scores it. The warp that meets the
-        // program's first tile enqueues it once; without a deep list it cannot be scored.
-        if (J.deep_list) {
-            if (t == 0 && lane == 0) J.deep_list[atomicAdd(J.deep_count, 1)] = static_cast<int32_t>(p);
-            return 1;
+    constexpr bool kPtx = sizeof(T) == 4 && (K == 4 || K == 8);   // the inline-PTX loops
+    Packed pk;
+    bool have = false;
+    if constexpr (D == kDepthFast) {
+        // Packed once for the call by the packing kernel: copy its tokens (the deep ones are
+        // on the deep list already).
+        if (J.packed) {
+            const uint32_t m = J.pmeta[q];
+            if (m != kPackNone) {
+                pk.n = static_cast<int>(m & 0xffffu);
+                pk.malformed = (m & kPackMalformed) != 0;
+                pk.deep = (m & kPackDeep) != 0;
+                pk.const_bad = (m & kPackConstBad) != 0;
+                if (pk.deep && J.deep_list) return 1;
+                if (!pk.malformed && !pk.deep) {
+                    const uint2 *src = J.packed + J.poff[q];
+                    for (int i = lane; i <= pk.n; i += 32) pbuf[i] = src[i];
+                    __syncwarp();
+                }
+                have = true;
+            }
         }
     }
-    if constexpr (sizeof(T) == 4 && K == 4) {
-        // Bits 24-28 of each token: the handler id of the token after it (the 4-case
-        // interpreter branches on it while it loads that token). Each round reads, then writes.
-        for (int base = 0; base < pk.n; base += 32) {
-            const int i = base + lane;
-            const uint32_t nh = i < pk.n ? (pbuf[i + 1].x & 31u) : 0u;
-            __syncwarp();
-            if (i < pk.n) pbuf[i].x |= nh << 24;
-            __syncwarp();
+    if (!have) {
+        const int64_t off = J.offs[p];
+        pk = pack_program<T, D>(J.ops + off, J.consts + off, J.lens[p], J.d, pbuf, lane);
+        if (pk.deep) {
+            // Deeper than this pass's stack: the deep pass scores it. The warp that meets the
+            // program's first tile enqueues it once; without a deep list it cannot be scored.
+            if (J.deep_list) {
+                if (t == 0 && lane == 0) J.deep_list[atomicAdd(J.deep_count, 1)] = static_cast<int32_t>(p);
+                return 1;
+            }
+        }
+        if constexpr (kPtx) {
+            // Bits 24-28 of each token: the handler id of the token after it (the inline-PTX
+            // interpreters branch on it while they load that token). Each round reads, then
+            // writes.
+            for (int base = 0; base < pk.n; base += 32) {
+                const int i = base + lane;
+                const uint32_t nh = i < pk.n ? (pbuf[i + 1].x & 31u) : 0u;
+                __syncwarp();
+                if (i < pk.n) pbuf[i].x |= nh << 24;
+                __syncwarp();
+            }
         }
     }
 
@@ -394,7 +403,7 @@ __device__ __forceinline__ int process_program(const JobDev &J, int64_t p, int t
         return part + (static_cast<int64_t>(f) * tiles + t) * P + p;
     };
     if (pk.malformed || pk.deep) {
-        if (lane == 0) *field(J.kind == kFitMse ? kTileFlags : kfFlags) = TF_MALFORMED;
+        if (lane == 0) *field(FIT ? kfFlags : kTileFlags) = TF_MALFORMED;
         return 0;
     }
     const int64_t tstart = static_cast<int64_t>(t) * tile;
@@ -404,14 +413,20 @@ __device__ __forceinline__ int process_program(const JobDev &J, int64_t p, int t
     TileValues<T, K> vals;
     vals.buf = fbuf;
     bool anybad = pk.const_bad;
-    if constexpr (kRegs) {   // one pass: the whole 256-case tile
-        bool bad[8];
-        run_program_ptx8(smem_addr(pbuf), smem_addr(xs + lane * 4), smem_addr(stk + lane * 4),
-                         vals.r, bad);
+    if constexpr (sizeof(T) == 4 && K == 8) {
+        static_assert(CH == kBox, "a pass of the 8-case loop is one staged box");
+        for (int c0 = 0; c0 < nval; c0 += CH) {
+            const float *xrow = xs + (c0 / kBox) * rows * kBox + lane * 4;
+            float f[8];
+            bool bad[8];
+            run_program_ptx8(smem_addr(pbuf), smem_addr(xrow), tstk, f, bad);
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            if (bad[j] && (j >> 2) * 128 + lane * 4 + (j & 3) < nval) anybad = true;
-            if (J.kind != kFitMse && bad[j]) vals.r[j] = __int_as_float(0x7fc00000);
+            for (int j = 0; j < 8; ++j) {
+                if (FIT && bad[j]) f[j] = __int_as_float(0x7fc00000);
+                if (bad[j] && c0 + (j >> 2) * 128 + lane * 4 + (j & 3) < nval) anybad = true;
+            }
+            *reinterpret_cast<float4 *>(fbuf + c0 + lane * 4) = make_float4(f[0], f[1], f[2], f[3]);
+            *reinterpret_cast<float4 *>(fbuf + c0 + 128 + lane * 4) = make_float4(f[4], f[5], f[6], f[7]);
         }
     } else {
         for (int c0 = 0; c0 < nval; c0 += CH) {
@@ -423,7 +438,7 @@ __device__ __forceinline__ int process_program(const JobDev &J, int64_t p, int t
             else
                 run_program<T, K>(smem_addr(pbuf), pk.n, smem_addr(xrow),
                                   smem_addr(stk + lane * K), f, bad);
-            if (J.kind != kFitMse) {   // the paper's fitness: invalid cases become NaN
+            if constexpr (FIT) {   // the paper's fitness: invalid cases become NaN
 #pragma unroll
                 for (int j = 0; j < K; ++j)
                     if (bad[j]) f[j] = static_cast<T>(__int_as_float(0x7fc00000));
@@ -447,7 +462,7 @@ __device__ __forceinline__ int process_program(const JobDev &J, int64_t p, int t
             }
         });
     }
-    if (J.kind != kFitMse) {
+    if constexpr (FIT) {
         fit_tile_stats<T, K>(J, nval, pk.const_bad, vals, xs, lane, field);
         return 0;
     }
@@ -643,10 +658,22 @@ __device__ __forceinline__ int process_program(const JobDev &J, int64_t p, int t
 // fits 32 warps; the 8-case and FP64 paths get 16 warps (128 registers).
 // The deep pass (D = 32) of the 4-case path has 16 consumer warps: 128 tensor-memory columns
 // each fill the 512 columns.
+// q: the program's position in the work order, p its index.
+template <typename T, int K, int D>
+__device__ __forceinline__ int process_program(const JobDev &J, int64_t q, int64_t p, int t,
+                                               int tile, const float *xs, uint2 *pbuf, T *fbuf,
+                                               T *stk, uint32_t tstk, int lane) {
+    if (J.kind == kFitMse)
+        return process_program_kind<T, K, D, false>(J, q, p, t, tile, xs, pbuf, fbuf, stk, tstk, lane);
+    return process_program_kind<T, K, D, true>(J, q, p, t, tile, xs, pbuf, fbuf, stk, tstk, lane);
+}
+
 template <typename T, int K, int D>
 struct KernelThreads {
+    // FP32 with the stack in TMEM: 4 cases, 16 values: 31 consumer warps (64 columns each);
+    // 4 cases, 32 values, or 8 cases, 16 values: 16 warps (128 columns each)
     static constexpr int value = sizeof(T) != 4 ? 512 : (K == 4 && D > 16) ? 544 :
-                                 K == 2 ? 1024 : K == 4 ? 1024 : 512;
+                                 K == 8 ? 544 : 1024;
 };
 
 // Finalize: merge each program's tiles in a fixed order in fp64 (Chan et al.'s pairwise

@@ -69,7 +69,7 @@ score_kernel(const __grid_constant__ LaunchParams<MAXJ> prm) {
     constexpr bool kTmem = kTmemStackPath<T, K>;
     uint32_t *tmem_base = reinterpret_cast<uint32_t *>(smem + 32);
     if constexpr (kTmem) {
-        if (warp == 0) tmem_alloc(tmem_base, tmem_columns(NW, D));
+        if (warp == 0) tmem_alloc(tmem_base, tmem_columns(NW, D, K));
         tmem_fence_before_sync();
     }
     if (threadIdx.x == 0) {
@@ -86,7 +86,7 @@ score_kernel(const __grid_constant__ LaunchParams<MAXJ> prm) {
         tmem_fence_after_sync();
         // lane quarter warp % 4 (TMEM lane field, bits 16-31), column slot warp / 4
         tstk = *tmem_base + (static_cast<uint32_t>(warp & 3) << 21) +
-               static_cast<uint32_t>((warp >> 2) * tmem_cols_per_warp(D));
+               static_cast<uint32_t>((warp >> 2) * tmem_cols_per_warp(D, K));
     }
 
     if (warp == NW) {
@@ -160,7 +160,7 @@ score_kernel(const __grid_constant__ LaunchParams<MAXJ> prm) {
             const int64_t q = p0 + idx;
             if (q >= p1) break;
             const int64_t p = order ? static_cast<int64_t>(order[q]) : q;
-            process_program<T, K, D>(J, p, s.tile, tile, xs, pbuf, fbuf, stk, tstk, lane);
+            process_program<T, K, D>(J, q, p, s.tile, tile, xs, pbuf, fbuf, stk, tstk, lane);
         }
         __syncwarp();
         if (lane == 0) mbar_arrive(&empty[b]);
@@ -172,7 +172,7 @@ score_kernel(const __grid_constant__ LaunchParams<MAXJ> prm) {
         asm volatile("bar.sync 1, %0;" ::"r"(NW * 32) : "memory");
         if (warp == 0) {
             tmem_fence_after_sync();
-            tmem_dealloc(*tmem_base, tmem_columns(NW, D));
+            tmem_dealloc(*tmem_base, tmem_columns(NW, D, K));
         }
     }
 }
@@ -212,7 +212,7 @@ static int fit_warps(int xbuf_floats, int tile, int nw_cap) {
 template <typename T, int K, int D, int MAXJ>
 static cudaError_t launch_pass(const LaunchParams<MAXJ> &prm, int nw, int grid,
                                cudaStream_t stream) {
-    const size_t smem = SmemLayout<T, K, D>::total(prm.xbuf_floats, prm.tile, nw);
+    const size_t smem = one_cta_per_sm(SmemLayout<T, K, D>::total(prm.xbuf_floats, prm.tile, nw));
     auto kern = score_kernel<T, K, D, MAXJ>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          static_cast<int>(smem));

@@ -57,7 +57,7 @@ serve_kernel(const __grid_constant__ ServeParams prm) {
     constexpr bool kTmem = kTmemStackPath<T, K>;
     uint32_t *tmem_base = reinterpret_cast<uint32_t *>(smem + 32);
     if constexpr (kTmem) {
-        if (warp == 0) tmem_alloc(tmem_base, tmem_columns(NW, D));
+        if (warp == 0) tmem_alloc(tmem_base, tmem_columns(NW, D, K));
         tmem_fence_before_sync();
     }
     if (threadIdx.x == 0) {
@@ -72,7 +72,7 @@ serve_kernel(const __grid_constant__ ServeParams prm) {
     if constexpr (kTmem) {
         tmem_fence_after_sync();
         tstk = *tmem_base + (static_cast<uint32_t>(warp & 3) << 21) +
-               static_cast<uint32_t>((warp >> 2) * tmem_cols_per_warp(D));
+               static_cast<uint32_t>((warp >> 2) * tmem_cols_per_warp(D, K));
     }
 
     if (warp == NW) {
@@ -175,7 +175,7 @@ serve_kernel(const __grid_constant__ ServeParams prm) {
             const int64_t q = p0 + idx;
             if (q >= p1) break;
             const int64_t p = J.order ? static_cast<int64_t>(J.order[q]) : q;
-            const int deep = process_program<T, K, D>(J, p, s.tile, tile, xs, pbuf, fbuf, stk,
+            const int deep = process_program<T, K, D>(J, q, p, s.tile, tile, xs, pbuf, fbuf, stk,
                                                       tstk, lane);
             if (lane == 0) {
                 __threadfence();   // this unit's partials before its count
@@ -204,7 +204,7 @@ serve_kernel(const __grid_constant__ ServeParams prm) {
         asm volatile("bar.sync 1, %0;" ::"r"(NW * 32) : "memory");
         if (warp == 0) {
             tmem_fence_after_sync();
-            tmem_dealloc(*tmem_base, tmem_columns(NW, D));
+            tmem_dealloc(*tmem_base, tmem_columns(NW, D, K));
         }
     }
 }
@@ -215,7 +215,7 @@ static cudaError_t launch_serve_impl(const ServeParams &prm, cudaStream_t s) {
     while (nw > 1 &&
            SmemLayout<T, K, kDepthFast>::total(prm.xbuf_floats, prm.tile, nw) > kSmemBudget)
         --nw;
-    const size_t smem = SmemLayout<T, K, kDepthFast>::total(prm.xbuf_floats, prm.tile, nw);
+    const size_t smem = one_cta_per_sm(SmemLayout<T, K, kDepthFast>::total(prm.xbuf_floats, prm.tile, nw));
     auto kern = serve_kernel<T, K>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          static_cast<int>(smem));

@@ -18,6 +18,9 @@
 //             Only valid operands matter (finite, |x| <= 1e30): the results for others are
 //             never used, because the program is already invalid.
 //
+// sincos_fast2 and plog2 take two arguments at once with the paired FP32 instructions, with
+// the same bits as the one-argument forms.
+//
 // P, Q and L are polynomials whose coefficients gen_poly.py (beside this file) fits to
 // relative error and rounds to fp32; with exact evaluation their maximum relative errors are
 // 3.6e-9, 3.9e-9 and 6.6e-9 (under 0.1 ulp). Each result is a function of its argument alone,
@@ -92,6 +95,46 @@ __device__ __forceinline__ void sincos4(float &t0, float &t1, float &t2, float &
     }
 }
 
+// The same on two arguments at once with the paired FP32 instructions (FFMA2, FADD2, FMUL2:
+// each half rounded exactly like its scalar form), so each result has the bits sincos_fast
+// gives it.
+__device__ __forceinline__ float2 f2(float c) { return make_float2(c, c); }
+
+__device__ __forceinline__ float2 sincos_fast2(float2 x, int qo) {
+    const float2 t = __ffma2_rn(x, f2(kTwoOverPi), f2(kRoundMagic));
+    const float2 kf = __fadd2_rn(t, f2(-kRoundMagic));
+    float2 r = __ffma2_rn(kf, f2(-kPio2C1), x);
+    r = __ffma2_rn(kf, f2(-kPio2C2), r);
+    r = __ffma2_rn(kf, f2(-kPio2C3), r);
+    const float2 s = __fmul2_rn(r, r);
+    const float2 ps = __ffma2_rn(
+        __ffma2_rn(__ffma2_rn(f2(kSinP3), s, f2(kSinP2)), s, f2(kSinP1)), s, f2(kSinP0));
+    const float2 pc = __ffma2_rn(
+        __ffma2_rn(__ffma2_rn(f2(kCosQ3), s, f2(kCosQ2)), s, f2(kCosQ1)), s, f2(kCosQ0));
+    const float2 vs = __ffma2_rn(__fmul2_rn(r, s), ps, r);
+    const float2 vc = __ffma2_rn(s, pc, f2(1.0f));
+    const int qx = (__float_as_int(t.x) - kRoundMagicBits) + qo;
+    const int qy = (__float_as_int(t.y) - kRoundMagicBits) + qo;
+    const float vx = (qx & 1) ? vc.x : vs.x;
+    const float vy = (qy & 1) ? vc.y : vs.y;
+    return make_float2(__int_as_float(__float_as_int(vx) ^ ((qx & 2) << 30)),
+                       __int_as_float(__float_as_int(vy) ^ ((qy & 2) << 30)));
+}
+
+// sin or cos of the four values of two pairs, large arguments as in sincos4.
+__device__ __forceinline__ void sincos4_paired(float2 &a, float2 &b, int qo) {
+    const float2 a0 = a, b0 = b;
+    a = sincos_fast2(a0, qo);
+    b = sincos_fast2(b0, qo);
+    const float big = (fabsf(a0.x) + fabsf(a0.y)) + (fabsf(b0.x) + fabsf(b0.y));
+    if (!(big <= kSinCosFastLimit)) {
+        if (!(fabsf(a0.x) <= kSinCosFastLimit)) a.x = sincos_slow(a0.x, qo);
+        if (!(fabsf(a0.y) <= kSinCosFastLimit)) a.y = sincos_slow(a0.y, qo);
+        if (!(fabsf(b0.x) <= kSinCosFastLimit)) b.x = sincos_slow(b0.x, qo);
+        if (!(fabsf(b0.y) <= kSinCosFastLimit)) b.y = sincos_slow(b0.y, qo);
+    }
+}
+
 // ---------------------------------------------------------------- protected log
 __device__ __forceinline__ float plog_dev(float x) {
     const float a = fabsf(x);
@@ -107,6 +150,27 @@ __device__ __forceinline__ float plog_dev(float x) {
     const float ef = __int_as_float(kRoundMagicBits + e) - kRoundMagic;   // exact for |e| < 2^22
     const float v = fmaf(ef, kLn2Hi, fmaf(ef, kLn2Lo, lnm));
     return a > kLogTiny ? v : 0.0f;
+}
+
+// The protected log of two arguments at once, the floating-point steps of plog_dev paired.
+__device__ __forceinline__ float2 plog2(float2 x) {
+    const float ax = fabsf(x.x), ay = fabsf(x.y);
+    const uint32_t ix = __float_as_uint(ax) + (0x3f800000u - 0x3f3504f4u);
+    const uint32_t iy = __float_as_uint(ay) + (0x3f800000u - 0x3f3504f4u);
+    const int ex = static_cast<int>(ix >> 23) - 127, ey = static_cast<int>(iy >> 23) - 127;
+    const float2 f = __fadd2_rn(make_float2(__uint_as_float((ix & 0x007fffffu) + 0x3f3504f4u),
+                                            __uint_as_float((iy & 0x007fffffu) + 0x3f3504f4u)),
+                                f2(-1.0f));
+    float2 l = __ffma2_rn(__ffma2_rn(__ffma2_rn(f2(kLogL7), f, f2(kLogL6)), f, f2(kLogL5)), f,
+                          f2(kLogL4));
+    l = __ffma2_rn(__ffma2_rn(__ffma2_rn(__ffma2_rn(l, f, f2(kLogL3)), f, f2(kLogL2)), f,
+                              f2(kLogL1)), f, f2(kLogL0));
+    const float2 lnm = __ffma2_rn(__fmul2_rn(f, f), __ffma2_rn(f, l, f2(-0.5f)), f);
+    const float2 ef = __fadd2_rn(make_float2(__int_as_float(kRoundMagicBits + ex),
+                                             __int_as_float(kRoundMagicBits + ey)),
+                                 f2(-kRoundMagic));
+    const float2 v = __ffma2_rn(ef, f2(kLn2Hi), __ffma2_rn(ef, f2(kLn2Lo), lnm));
+    return make_float2(ax > kLogTiny ? v.x : 0.0f, ay > kLogTiny ? v.y : 0.0f);
 }
 
 }  // namespace beagle

@@ -423,3 +423,30 @@ def test_eval_outputs_within_error_bound_per_case():
                                    dl[bad][:3])
             checked += len(g)
         assert checked > 300000
+
+
+@pytest.mark.parametrize("cases", [4, 8])
+def test_deep_well_conditioned_programs(cases):
+    """Deep programs whose values stay well conditioned (positive leaves; +, x and squaring
+    only), so that nearly all fall in the strict set: the deep pass (32-value stack) within
+    1e-5 of both oracles (1e-12 on the FP64 path), not only inside the error envelope."""
+    rng = np.random.default_rng(60 + cases)
+    d, N = 3, 1100
+    X = rng.uniform(0.5, 1.5, (d, N)).astype(np.float32)
+    y = (np.sin(3 * X[0]) + X[1] - X[2]).astype(np.float32)
+    progs = S.gen_programs(rng, 400, 56, 100, d, depth_cap=32, weights=(0.68, 0.02, 0.3),
+                           unary=(S.SQUARE,), binary=(S.ADD, S.MUL), const_lo=0.5, const_hi=1.5)
+    depth = np.array([S.max_depth(progs.program(p)[0]) for p in range(progs.P)])
+    assert (depth > 16).sum() >= 200, (depth > 16).sum()
+    refs = parity.references(progs, X, y)
+    beagle.set_launch_config(cases_per_lane=cases)
+    try:
+        g32 = run_gpu(progs, X, y, "fp32c")
+        assert not np.any(g32[2] & beagle.FLAG_MALFORMED)
+        stats = parity.check_fp32(g32, refs, min_strict=0.95, name=f"deep-wc-{cases}")
+        print(stats)
+        if cases == 4:
+            g64 = run_gpu(progs, X, y, "fp64")
+            parity.check_fp64(g64, refs, min_strict=0.95, name="deep-wc")
+    finally:
+        beagle.reset_launch_config()
