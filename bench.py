@@ -37,10 +37,10 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "GPoPs (node-evals/s) FP32-compensated vs plain FP64 at ≤1e-5 rel err; p50/p99"
-# kernels one scoring call launches: length order, the persistent scoring kernel's fast pass
-# and deep pass (programs deeper than 16 values; it exits at once when there are none), fp64
-# finalize
-LAUNCHES_PER_CALL = 4
+# kernels one scoring call launches: length order, packing (each program translated into
+# handlers once), the persistent scoring kernel's fast pass and deep pass (programs deeper
+# than 16 values; it exits at once when there are none), fp64 finalize
+LAUNCHES_PER_CALL = 5
 C1_DESC = ("c1-small-1024: P=1024 programs, length U{8..32}, d=2, N=1024 cases, X~U[-3,3], "
            "y = x0 sin(x1) + x0^2/2; MSE")
 C2_DESC = ("c2-population-100k: P=100000 programs, length U{16..128}, d=5, N=1024 cases, "
@@ -152,11 +152,73 @@ ALGO_UNITS = {1: (1, 0, 1), 2: (1, 0, 1), 3: (1, 0, 1), 10: (1, 0, 1),
 LANES_PER_SM_CLK = {"fp32": 128, "mufu": 32, "alu": 64, "issue": 128}
 
 
-def algorithmic_units(progs_list):
-    """Lane operations of each pipe over populations [(programs, N)]."""
+def folded_op_counts(progs):
+    """Per opcode, the operators the packing kernel folds (constant subexpressions, evaluated
+    once per call instead of on every case): the constness of every stack value followed
+    through all programs at once, token position by token position. Programs that use the
+    COPY/PASTE registers are not folded (as on the device)."""
+    from paper_2607_06731_gb300 import synth as S
+    P = progs.P
+    out = np.zeros(256, np.int64)
+    if P == 0:
+        return out
+    L = progs.lengths.astype(np.int64)
+    offs = progs.offsets.astype(np.int64)
+    cst = np.zeros((P, 36), bool)
+    sp = np.zeros(P, np.int64)
+    regs = np.zeros(P, bool)
+    per = []
+    un = np.zeros(256, bool)
+    for op in list(range(S.SIN, S.SQUARE + 1)) + list(range(S.POW + 1, S.TANH + 1)):
+        un[op] = True
+    bn = np.zeros(256, bool)
+    bn[[S.ADD, S.SUB, S.MUL, S.PDIV, S.POW]] = True
+    for t in range(int(L.max())):
+        act = np.nonzero(L > t)[0]
+        op = progs.ops[offs[act] + t].astype(np.int64)
+        s_ = sp[act]
+        isconst = op == S.CONST
+        isvar = (op >= S.LOAD0) & (op < S.LOAD0 + 16)
+        regs[act[(op >= S.COPY0) & (op < S.PASTE0 + 16)]] = True
+        # leaves
+        lf = isconst | isvar
+        cst[act[lf], np.minimum(s_[lf], 35)] = isconst[lf]
+        # unary: folded when the top is constant
+        u = un[op]
+        fu = u & cst[act, np.maximum(s_ - 1, 0)]
+        # binary: folded when both operands are constant; the result is constant then
+        b = bn[op]
+        both = cst[act, np.maximum(s_ - 1, 0)] & cst[act, np.maximum(s_ - 2, 0)]
+        fb = b & both
+        cst[act[b], np.maximum(s_[b] - 2, 0)] = both[b]
+        # DUP / SWAP / DEL on constants
+        dup = op == S.DUP
+        fd = dup & cst[act, np.maximum(s_ - 1, 0)]
+        cst[act[dup], np.minimum(s_[dup], 35)] = cst[act[dup], np.maximum(s_[dup] - 1, 0)]
+        sw = op == S.SWAP
+        fs = sw & both
+        a1 = cst[act[sw], np.maximum(s_[sw] - 1, 0)].copy()
+        cst[act[sw], np.maximum(s_[sw] - 1, 0)] = cst[act[sw], np.maximum(s_[sw] - 2, 0)]
+        cst[act[sw], np.maximum(s_[sw] - 2, 0)] = a1
+        dl = op == S.DEL
+        fdl = dl & cst[act, np.maximum(s_ - 1, 0)]
+        sp[act] += lf.astype(np.int64) + dup - b - dl
+        f = fu | fb | fd | fs | fdl
+        per.append((act[f], op[f]))
+    for idx, op in per:
+        keep = ~regs[idx]
+        np.add.at(out, op[keep], 1)
+    return out
+
+
+def algorithmic_units(progs_list, folded=True):
+    """Lane operations of each pipe over populations [(programs, N)], of the operators the
+    interpreter runs (the folded constant subexpressions left out unless folded=False)."""
     tot = {"fp32": 0.0, "mufu": 0.0, "alu": 0.0}
     for progs, N in progs_list:
         counts = np.bincount(progs.ops, minlength=256).astype(np.float64)
+        if folded:
+            counts -= folded_op_counts(progs)
         for op, (f, m, a) in ALGO_UNITS.items():
             tot["fp32"] += counts[op] * N * f
             tot["mufu"] += counts[op] * N * m

@@ -12,9 +12,11 @@
 // its scalar form, so the results are bit-identical to scalar code): the top of stack is two
 // pairs, %0 = cases (4l, 4l+1) and %1 = (4l+2, 4l+3) of lane l.
 //
-// sin, cos, exp, the protected log, POW and the rest of Table 3's transcendentals leave the
-// loop with their handler id; the caller applies them to the top of stack (transcend.cuh's
-// branch-free sin, cos and log on pairs; CUDA's expf and the others) and re-enters.
+// sin, cos and the protected log run in the loop (transcend.cuh's branch-free forms, the
+// floating-point steps paired, with the same bits). exp, POW and the rest of Table 3's
+// transcendentals, and sin and cos of arguments above 65536, leave the loop with their
+// handler id; the caller applies them to the top of stack (CUDA's expf and the others) and
+// re-enters.
 #pragma once
 
 #include "score.cuh"
@@ -36,12 +38,74 @@ namespace beagle {
     "abs.f32 z, d0;\n\tsetp.gt.f32 q0, z, 0f3A83126F;\n\t"                                 \
     "abs.f32 z, d1;\n\tsetp.gt.f32 q1, z, 0f3A83126F;\n\t"                                 \
     "rcp.approx.ftz.f32 d0, d0;\n\trcp.approx.ftz.f32 d1, d1;\n\tmov.b64 Y, {d0, d1};\n\t"  \
-    "mul.rn.f32x2 ND, " DEN ", M1;\n\t"                                                     \
-    "fma.rn.f32x2 E, ND, Y, ONE;\n\tfma.rn.f32x2 Y, E, Y, Y;\n\t"                           \
+    "mov.b64 KA, " BG_PTX_PAIR(BG_K_NONE) ";\n\tmul.rn.f32x2 ND, " DEN ", KA;\n\t"             \
+    "mov.b64 KA, " BG_PTX_PAIR(BG_K_ONE) ";\n\t"                                               \
+    "fma.rn.f32x2 E, ND, Y, KA;\n\tfma.rn.f32x2 Y, E, Y, Y;\n\t"                            \
     "mul.rn.f32x2 Z, " NUM ", Y;\n\tfma.rn.f32x2 E, ND, Z, " NUM ";\n\t"                     \
     "fma.rn.f32x2 Z, E, Y, Z;\n\t"                                                          \
     "mov.b64 {d0, d1}, Z;\n\tselp.f32 d0, d0, 0f3F800000, q0;\n\t"                          \
     "selp.f32 d1, d1, 0f3F800000, q1;\n\tmov.b64 " DST ", {d0, d1};\n\t"
+
+// sin or cos of one pair X (transcend.cuh's sincos_fast step for step, the floating-point
+// steps paired): t = x 2/pi + 1.5 2^23, k = t - 1.5 2^23, r = x - k pi/2 in three parts,
+// both polynomials in s = r^2, then per half the quadrant q = bits(t) - bits(1.5 2^23) + qo
+// (qo in the register qoff with the magic subtracted): an odd q takes the cosine, bit 1 of q
+// flips the sign.
+#define BG4_SINCOS2(X)                                                                     \
+    "mov.b64 KA, " BG_PTX_PAIR(BG_K_TWO_OVER_PI) ";\n\tmov.b64 KB, " BG_PTX_PAIR(BG_K_MAGIC) ";\n\t" \
+    "fma.rn.f32x2 TQ, " X ", KA, KB;\n\t"                                                  \
+    "mov.b64 KA, " BG_PTX_PAIR(BG_K_NMAGIC) ";\n\tadd.rn.f32x2 E, TQ, KA;\n\t"               \
+    "mov.b64 KA, " BG_PTX_PAIR(BG_K_NPIO2_C1) ";\n\tfma.rn.f32x2 Z, E, KA, " X ";\n\t"        \
+    "mov.b64 KA, " BG_PTX_PAIR(BG_K_NPIO2_C2) ";\n\tfma.rn.f32x2 Z, E, KA, Z;\n\t"            \
+    "mov.b64 KA, " BG_PTX_PAIR(BG_K_NPIO2_C3) ";\n\tfma.rn.f32x2 Z, E, KA, Z;\n\t"            \
+    "mul.rn.f32x2 Y, Z, Z;\n\t"                                                            \
+    "mov.b64 KA, " BG_PTX_PAIR(BG_K_SIN_P3) ";\n\tmov.b64 KB, " BG_PTX_PAIR(BG_K_SIN_P2) ";\n\t" \
+    "fma.rn.f32x2 A01, KA, Y, KB;\n\t"                                                     \
+    "mov.b64 KB, " BG_PTX_PAIR(BG_K_SIN_P1) ";\n\tfma.rn.f32x2 A01, A01, Y, KB;\n\t"          \
+    "mov.b64 KB, " BG_PTX_PAIR(BG_K_SIN_P0) ";\n\tfma.rn.f32x2 A01, A01, Y, KB;\n\t"          \
+    "mov.b64 KA, " BG_PTX_PAIR(BG_K_COS_Q3) ";\n\tmov.b64 KB, " BG_PTX_PAIR(BG_K_COS_Q2) ";\n\t" \
+    "fma.rn.f32x2 A23, KA, Y, KB;\n\t"                                                     \
+    "mov.b64 KB, " BG_PTX_PAIR(BG_K_COS_Q1) ";\n\tfma.rn.f32x2 A23, A23, Y, KB;\n\t"          \
+    "mov.b64 KB, " BG_PTX_PAIR(BG_K_COS_Q0) ";\n\tfma.rn.f32x2 A23, A23, Y, KB;\n\t"          \
+    "mul.rn.f32x2 E, Z, Y;\n\tfma.rn.f32x2 A01, E, A01, Z;\n\t"                            \
+    "mov.b64 KB, " BG_PTX_PAIR(BG_K_ONE) ";\n\tfma.rn.f32x2 A23, Y, A23, KB;\n\t"             \
+    "mov.b64 {u0, u1}, TQ;\n\tmov.b64 {w0, w1}, A01;\n\tmov.b64 {w2, w3}, A23;\n\t"         \
+    "add.s32 u0, u0, qoff;\n\tadd.s32 u1, u1, qoff;\n\t"                                   \
+    "bfe.s32 v, u0, 0, 1;\n\tlop3.b32 w0, w0, w2, v, 0xD8;\n\t"                            \
+    "bfe.s32 v, u1, 0, 1;\n\tlop3.b32 w1, w1, w3, v, 0xD8;\n\t"                            \
+    "shl.b32 u0, u0, 30;\n\tlop3.b32 w0, w0, u0, 0x80000000, 0x78;\n\t"                    \
+    "shl.b32 u1, u1, 30;\n\tlop3.b32 w1, w1, u1, 0x80000000, 0x78;\n\t"                    \
+    "mov.b64 " X ", {w0, w1};\n\t"
+// The protected log of one pair X (plog_dev step for step, the floating-point steps paired):
+// |x| = m 2^e with m in [b, 2b), b just above sqrt(1/2), from integer arithmetic on the bits;
+// f = m - 1; ln m = f + f^2 (-1/2 + f L(f)); plus e ln 2 in two parts; 0 where |x| <= 1e-3.
+#define BG4_PLOG2(X)                                                                       \
+    "mov.b64 {d0, d1}, " X ";\n\tabs.f32 d0, d0;\n\tabs.f32 d1, d1;\n\t"                    \
+    "mov.b32 u0, d0;\n\tmov.b32 u1, d1;\n\t"                                               \
+    "add.u32 u0, u0, 0x004AFB0C;\n\tadd.u32 u1, u1, 0x004AFB0C;\n\t"                       \
+    "shr.u32 w0, u0, 23;\n\tadd.u32 w0, w0, 0x4B3FFF81;\n\t"                               \
+    "shr.u32 w1, u1, 23;\n\tadd.u32 w1, w1, 0x4B3FFF81;\n\t"                               \
+    "and.b32 u0, u0, 0x007FFFFF;\n\tadd.u32 u0, u0, 0x3F3504F4;\n\t"                       \
+    "and.b32 u1, u1, 0x007FFFFF;\n\tadd.u32 u1, u1, 0x3F3504F4;\n\t"                       \
+    "mov.b64 Z, {u0, u1};\n\tmov.b64 KA, " BG_PTX_PAIR(BG_K_NONE) ";\n\tadd.rn.f32x2 Z, Z, KA;\n\t" \
+    "mov.b64 TQ, {w0, w1};\n\tmov.b64 KA, " BG_PTX_PAIR(BG_K_NMAGIC) ";\n\tadd.rn.f32x2 TQ, TQ, KA;\n\t" \
+    "mov.b64 KA, " BG_PTX_PAIR(BG_K_LOG_L7) ";\n\tmov.b64 KB, " BG_PTX_PAIR(BG_K_LOG_L6) ";\n\t" \
+    "fma.rn.f32x2 Y, KA, Z, KB;\n\t"                                                       \
+    "mov.b64 KB, " BG_PTX_PAIR(BG_K_LOG_L5) ";\n\tfma.rn.f32x2 Y, Y, Z, KB;\n\t"              \
+    "mov.b64 KB, " BG_PTX_PAIR(BG_K_LOG_L4) ";\n\tfma.rn.f32x2 Y, Y, Z, KB;\n\t"              \
+    "mov.b64 KB, " BG_PTX_PAIR(BG_K_LOG_L3) ";\n\tfma.rn.f32x2 Y, Y, Z, KB;\n\t"              \
+    "mov.b64 KB, " BG_PTX_PAIR(BG_K_LOG_L2) ";\n\tfma.rn.f32x2 Y, Y, Z, KB;\n\t"              \
+    "mov.b64 KB, " BG_PTX_PAIR(BG_K_LOG_L1) ";\n\tfma.rn.f32x2 Y, Y, Z, KB;\n\t"              \
+    "mov.b64 KB, " BG_PTX_PAIR(BG_K_LOG_L0) ";\n\tfma.rn.f32x2 Y, Y, Z, KB;\n\t"              \
+    "mul.rn.f32x2 E, Z, Z;\n\t"                                                            \
+    "mov.b64 KB, " BG_PTX_PAIR(BG_K_NHALF) ";\n\tfma.rn.f32x2 Y, Z, Y, KB;\n\t"               \
+    "fma.rn.f32x2 Y, E, Y, Z;\n\t"                                                         \
+    "mov.b64 KA, " BG_PTX_PAIR(BG_K_LN2_LO) ";\n\tfma.rn.f32x2 Y, TQ, KA, Y;\n\t"             \
+    "mov.b64 KA, " BG_PTX_PAIR(BG_K_LN2_HI) ";\n\tfma.rn.f32x2 Y, TQ, KA, Y;\n\t"             \
+    "mov.b64 {a0, a1}, Y;\n\t"                                                             \
+    "setp.gt.f32 q0, d0, " BG_PTX_F32(BG_K_LOG_TINY) ";\n\tselp.f32 a0, a0, 0f00000000, q0;\n\t" \
+    "setp.gt.f32 q1, d1, " BG_PTX_F32(BG_K_LOG_TINY) ";\n\tselp.f32 a1, a1, 0f00000000, q1;\n\t" \
+    "mov.b64 " X ", {a0, a1};\n\t"
 
 // Operands: %0/%1 top of stack (2 pairs), %2-%5 validity trackers, %6/%7 current token words,
 // %8 shared address of the next token, %9 exit code (0 = program done, else the handler id of
@@ -80,13 +144,13 @@ namespace beagle {
     "{\n\t"                                                                                \
     ".reg .pred q0, q1;\n\t"                                                               \
     ".reg .b32 h, v, rp, xa;\n\t"                                                          \
-    ".reg .b64 A01, A23, C2, Y, ND, E, Z, ONE, M1;\n\t"                                     \
+    ".reg .b64 A01, A23, C2, Y, ND, E, Z, KA, KB, TQ;\n\t"                                  \
     ".reg .f32 t0, t1, t2, t3, a0, a1, a2, a3, z, d0, d1;\n\t"                             \
+    ".reg .b32 u0, u1, w0, w1, w2, w3, qoff, sccode;\n\t"                                  \
     "TBL_%=: .branchtargets PUSHX_%=, PUSHC_%=, DUP_%=, SWAP_%=, DEL_%=, ADDSUB_%=, "      \
     "MUL_%=, PDIV_%=, SIN_%=, COS_%=, EXP_%=, PLOG_%=, PSQRT_%=, SQUARE_%=, ADDSUBX_%=, "   \
     "MULX_%=, PDIVX_%=, ADDC_%=, MULC_%=, PDIVC_%=, END_%=, POW_%=, SIGN_%=, CUBE_%=, "     \
     "CBRT_%=, TAN_%=, ASIN_%=, ACOS_%=, ATAN_%=, TANH_%=, PASTE_%=, END_%=;\n\t"           \
-    "mov.b64 ONE, 0x3F8000003F800000;\n\tmov.b64 M1, 0xBF800000BF800000;\n\t"              \
     BG4_DISPATCH                                                                           \
     "PUSHX_%=:\n\t" BG4_ROW BG4_XA BG4_STROW "ld.shared.v2.b64 {%0, %1}, [xa];\n\t"         \
     BG4_DISPATCH                                                                           \
@@ -104,7 +168,21 @@ namespace beagle {
     "mul.rn.f32x2 %0, A01, %0;\n\tmul.rn.f32x2 %1, A23, %1;\n\t" BG4_TRACK BG4_DISPATCH    \
     "PDIV_%=:\n\t" BG4_ROW BG4_LDROW_A                                                     \
     BG4_PDIV2("%0", "A01", "%0") BG4_PDIV2("%1", "A23", "%1") BG4_TRACK BG4_DISPATCH       \
-    BG4_EXIT("SIN", 8) BG4_EXIT("COS", 9) BG4_EXIT("EXP", 10) BG4_EXIT("PLOG", 11)         \
+    /* sin and cos: arguments above 65536 in magnitude or NaN on any lane leave the loop   \
+       (the caller takes CUDA's sinf / cosf on those lanes); no tracking: the results of a    \
+       valid operand are bounded */                                                        \
+    "SIN_%=:\n\tmov.u32 qoff, 0xB4C00000;\n\tmov.u32 sccode, 8;\n\tbra.uni SC_%=;\n"          \
+    "COS_%=:\n\tmov.u32 qoff, 0xB4C00001;\n\tmov.u32 sccode, 9;\n"                            \
+    "SC_%=:\n\t" BG4_UNPACK                                                                 \
+    "abs.f32 z, t0;\n\tabs.f32 d0, t1;\n\tmax.NaN.f32 z, z, d0;\n\t"                          \
+    "abs.f32 d0, t2;\n\tmax.NaN.f32 z, z, d0;\n\tabs.f32 d0, t3;\n\tmax.NaN.f32 z, z, d0;\n\t"  \
+    "setp.gtu.f32 q0, z, " BG_PTX_F32(BG_K_SINCOS_LIMIT) ";\n\t"                              \
+    "vote.sync.any.pred q1, q0, 0xffffffff;\n\t@q1 bra.uni SCX_%=;\n\t"                      \
+    BG4_SINCOS2("%0") BG4_SINCOS2("%1") BG4_DISPATCH                                       \
+    "SCX_%=:\n\tmov.u32 %9, sccode;\n\tbra.uni OUT_%=;\n"                                     \
+    BG4_EXIT("EXP", 10)                                                                    \
+    /* the protected log: no tracking (|ln|v|| <= 69.1 for a valid operand) */              \
+    "PLOG_%=:\n\t" BG4_PLOG2("%0") BG4_PLOG2("%1") BG4_DISPATCH                            \
     "PSQRT_%=:\n\t" BG4_UNPACK                                                             \
     "abs.f32 t0, t0;\n\tsqrt.rn.f32 t0, t0;\n\tabs.f32 t1, t1;\n\tsqrt.rn.f32 t1, t1;\n\t" \
     "abs.f32 t2, t2;\n\tsqrt.rn.f32 t2, t2;\n\tabs.f32 t3, t3;\n\tsqrt.rn.f32 t3, t3;\n\t" \
@@ -132,7 +210,8 @@ namespace beagle {
     /* the rest of Table 3: SIGN (|v| unchanged, nothing to track), CUBE ((a a) a), PASTE  \
        (push the top, load the register's row, its index in the constant word) */          \
     BG4_EXIT("POW", 21)                                                                    \
-    "SIGN_%=:\n\t" "mul.rn.f32x2 %0, %0, M1;\n\tmul.rn.f32x2 %1, %1, M1;\n\t" BG4_DISPATCH \
+    "SIGN_%=:\n\tmov.b64 KA, " BG_PTX_PAIR(BG_K_NONE) ";\n\t"                                 \
+    "mul.rn.f32x2 %0, %0, KA;\n\tmul.rn.f32x2 %1, %1, KA;\n\t" BG4_DISPATCH                \
     "CUBE_%=:\n\t" "mul.rn.f32x2 A01, %0, %0;\n\tmul.rn.f32x2 A23, %1, %1;\n\t"             \
     "mul.rn.f32x2 %0, A01, %0;\n\tmul.rn.f32x2 %1, A23, %1;\n\t" BG4_TRACK BG4_DISPATCH    \
     BG4_EXIT("CBRT", 24) BG4_EXIT("TAN", 25) BG4_EXIT("ASIN", 26) BG4_EXIT("ACOS", 27)     \
@@ -268,5 +347,7 @@ __device__ __forceinline__ void run_program_ptx4(uint32_t prog, uint32_t xrow, u
 #undef BG4_LDROW_T
 #undef BG4_LDX_A
 #undef BG4_EXIT
+#undef BG4_SINCOS2
+#undef BG4_PLOG2
 
 }  // namespace beagle

@@ -56,8 +56,11 @@ struct OrderParams {
 cudaError_t launch_length_order(const OrderParams &prm, cudaStream_t s);
 // Pack every program of the jobs that carry a packed-token buffer (JobDev::packed), once per
 // call, for the fast pass's 16-value stack; programs deeper than that go to the deep lists.
+// On the FP32 path constant subexpressions are folded first, into fold_ops / fold_cs (as many
+// entries as the jobs' packed buffers, job j's from JobDev::fold_base), unless they are null.
 template <int MAXJ>
-cudaError_t launch_pack(const LaunchParams<MAXJ> &prm, int precision, cudaStream_t s);
+cudaError_t launch_pack(const LaunchParams<MAXJ> &prm, int precision, uint8_t *fold_ops,
+                        float *fold_cs, cudaStream_t s);
 
 // Opt-in CUDA-event timing of scoring-kernel launches (beagle_kernel_timing).
 bool timing_enabled();

@@ -77,13 +77,18 @@ beagle_status enqueue(const std::vector<Planned> &jobs, size_t b, size_t e, int 
         const int64_t c = P * kPackedPerProgram;
         return c < int64_t(0xfffffffe) ? c : int64_t(0xfffffffe);
     };
+    int64_t fold_entries = 0;   // folded-program scratch (FP32): one entry per packed token
     for (size_t i = b; i < e; ++i) {
         scratch += up256(jobs[i].part_bytes) + up256(sizeof(int32_t) * jobs[i].dev.P);
-        if (sort && !jobs[i].dev.order)
+        if (sort && !jobs[i].dev.order) {
             scratch += up256(sizeof(int32_t) * jobs[i].dev.P) +
                        up256(sizeof(uint2) * pack_cap(jobs[i].dev.P)) +
                        2 * up256(sizeof(uint32_t) * jobs[i].dev.P);
+            fold_entries += pack_cap(jobs[i].dev.P);
+        }
     }
+    if (precision != BEAGLE_FP32_COMPENSATED) fold_entries = 0;
+    scratch += up256(sizeof(float) * fold_entries) + up256(fold_entries);
     char *base = nullptr;
     cudaError_t err = cudaMallocAsync(reinterpret_cast<void **>(&base), scratch, s);
     if (err != cudaSuccess)
@@ -96,6 +101,11 @@ beagle_status enqueue(const std::vector<Planned> &jobs, size_t b, size_t e, int 
     prm.counter = reinterpret_cast<unsigned int *>(base + kHdrCounter);
     prm.error = reinterpret_cast<unsigned int *>(base + kHdrError);
     char *cur = base + kHdrBytes;
+    float *fold_cs = fold_entries ? reinterpret_cast<float *>(cur) : nullptr;
+    cur += up256(sizeof(float) * fold_entries);
+    uint8_t *fold_ops = fold_entries ? reinterpret_cast<uint8_t *>(cur) : nullptr;
+    cur += up256(fold_entries);
+    int64_t fold_next = 0;
     int64_t items = 0;
     int nj = 0;
     OrderParams op;
@@ -121,6 +131,8 @@ beagle_status enqueue(const std::vector<Planned> &jobs, size_t b, size_t e, int 
             prm.jobs[nj].packed = packed;
             prm.jobs[nj].poff = poff;
             prm.jobs[nj].pmeta = pmeta;
+            prm.jobs[nj].fold_base = fold_next;
+            fold_next += pack_cap(jobs[i].dev.P);
             op.lens[op.njobs] = jobs[i].dev.lens;
             op.order[op.njobs] = ord;
             op.poff[op.njobs] = poff;
@@ -139,7 +151,7 @@ beagle_status enqueue(const std::vector<Planned> &jobs, size_t b, size_t e, int 
     prm.xbuf_floats = xbuf_floats;
     apply_wait_settings(&prm.wait_limit_ns, &prm.stall_producer);
     cudaError_t le = launch_length_order(op, s);
-    if (le == cudaSuccess) le = launch_pack(prm, precision, s);
+    if (le == cudaSuccess) le = launch_pack(prm, precision, fold_ops, fold_cs, s);
     if (le == cudaSuccess) {
         if constexpr (MAXJ == 1) le = launch_score(prm, precision, cases, nw, grid, s);
         else le = launch_score_batch(prm, precision, cases, nw, grid, s);

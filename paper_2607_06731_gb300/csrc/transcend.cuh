@@ -46,11 +46,86 @@ constexpr float kLogL0 = 0x1.555554p-2f, kLogL1 = -0x1.000226p-2f, kLogL2 = 0x1.
                 kLogL6 = 0x1.0562e0p-3f, kLogL7 = -0x1.38ceaap-4f;
 constexpr float kLogTiny = 1e-3f;
 
+// The same constants as fp32 bit patterns (hex digits), for the inline-PTX interpreter loops:
+// BG_PTX_F32 gives a PTX fp32 immediate, BG_PTX_PAIR the 64-bit immediate of the pair (c, c).
+// Each is checked against its value above at compile time.
+#define BG_K_TWO_OVER_PI 3F22F983
+#define BG_K_PIO2_C1 3FC90FDB
+#define BG_K_PIO2_C2 B33BBD2E
+#define BG_K_PIO2_C3 A6F72CED
+#define BG_K_NPIO2_C1 BFC90FDB
+#define BG_K_NPIO2_C2 333BBD2E
+#define BG_K_NPIO2_C3 26F72CED
+#define BG_K_SIN_P0 BE2AAAAB
+#define BG_K_SIN_P1 3C088884
+#define BG_K_SIN_P2 B9500789
+#define BG_K_SIN_P3 36365C06
+#define BG_K_COS_Q0 BF000000
+#define BG_K_COS_Q1 3D2AAA9D
+#define BG_K_COS_Q2 BAB603AB
+#define BG_K_COS_Q3 37CC7918
+#define BG_K_SINCOS_LIMIT 47800000
+#define BG_K_LN2_HI 3F317218
+#define BG_K_LN2_LO B102E308
+#define BG_K_LOG_L0 3EAAAAAA
+#define BG_K_LOG_L1 BE800113
+#define BG_K_LOG_L2 3E4CD00F
+#define BG_K_LOG_L3 BE2A392A
+#define BG_K_LOG_L4 3E116C57
+#define BG_K_LOG_L5 BE06C1BE
+#define BG_K_LOG_L6 3E02B170
+#define BG_K_LOG_L7 BD9C6755
+#define BG_K_LOG_TINY 3A83126F
+#define BG_K_MAGIC 4B400000
+#define BG_K_NMAGIC CB400000
+#define BG_K_ONE 3F800000
+#define BG_K_NONE BF800000
+#define BG_K_NHALF BF000000
+#define BG_STR_(x) #x
+#define BG_STR(x) BG_STR_(x)
+#define BG_HEX_(h) 0x##h##u
+#define BG_HEX(h) BG_HEX_(h)
+#define BG_PTX_F32(h) "0f" BG_STR(h)
+#define BG_PTX_PAIR(h) "0x" BG_STR(h) BG_STR(h)
+#define BG_CHECK_BITS(v, h) static_assert(__builtin_bit_cast(unsigned, v) == BG_HEX(h), #v)
+BG_CHECK_BITS(kTwoOverPi, BG_K_TWO_OVER_PI);
+BG_CHECK_BITS(kPio2C1, BG_K_PIO2_C1);
+BG_CHECK_BITS(kPio2C2, BG_K_PIO2_C2);
+BG_CHECK_BITS(kPio2C3, BG_K_PIO2_C3);
+BG_CHECK_BITS(-kPio2C1, BG_K_NPIO2_C1);
+BG_CHECK_BITS(-kPio2C2, BG_K_NPIO2_C2);
+BG_CHECK_BITS(-kPio2C3, BG_K_NPIO2_C3);
+BG_CHECK_BITS(kSinP0, BG_K_SIN_P0);
+BG_CHECK_BITS(kSinP1, BG_K_SIN_P1);
+BG_CHECK_BITS(kSinP2, BG_K_SIN_P2);
+BG_CHECK_BITS(kSinP3, BG_K_SIN_P3);
+BG_CHECK_BITS(kCosQ0, BG_K_COS_Q0);
+BG_CHECK_BITS(kCosQ1, BG_K_COS_Q1);
+BG_CHECK_BITS(kCosQ2, BG_K_COS_Q2);
+BG_CHECK_BITS(kCosQ3, BG_K_COS_Q3);
+BG_CHECK_BITS(kSinCosFastLimit, BG_K_SINCOS_LIMIT);
+BG_CHECK_BITS(kLn2Hi, BG_K_LN2_HI);
+BG_CHECK_BITS(kLn2Lo, BG_K_LN2_LO);
+BG_CHECK_BITS(kLogL0, BG_K_LOG_L0);
+BG_CHECK_BITS(kLogL1, BG_K_LOG_L1);
+BG_CHECK_BITS(kLogL2, BG_K_LOG_L2);
+BG_CHECK_BITS(kLogL3, BG_K_LOG_L3);
+BG_CHECK_BITS(kLogL4, BG_K_LOG_L4);
+BG_CHECK_BITS(kLogL5, BG_K_LOG_L5);
+BG_CHECK_BITS(kLogL6, BG_K_LOG_L6);
+BG_CHECK_BITS(kLogL7, BG_K_LOG_L7);
+BG_CHECK_BITS(kLogTiny, BG_K_LOG_TINY);
+BG_CHECK_BITS(1.0f, BG_K_ONE);
+BG_CHECK_BITS(-1.0f, BG_K_NONE);
+BG_CHECK_BITS(-0.5f, BG_K_NHALF);
+
 // ---------------------------------------------------------------- sin, cos (qo = 0 / 1)
 // Adding 1.5 * 2^23 rounds a float of magnitude below 2^22 to an integer held in the low
 // mantissa bits: the rounding and the conversion to int without the conversion unit.
 constexpr float kRoundMagic = 0x1.8p+23f;
 constexpr int kRoundMagicBits = 0x4b400000;
+BG_CHECK_BITS(kRoundMagic, BG_K_MAGIC);
+BG_CHECK_BITS(-kRoundMagic, BG_K_NMAGIC);
 
 __device__ __forceinline__ float sincos_fast(float x, int qo) {
     const float t = fmaf(x, kTwoOverPi, kRoundMagic);   // |x 2/pi| < 2^22 on this path

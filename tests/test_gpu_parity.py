@@ -450,3 +450,59 @@ def test_deep_well_conditioned_programs(cases):
             parity.check_fp64(g64, refs, min_strict=0.95, name="deep-wc")
     finally:
         beagle.reset_launch_config()
+
+
+def _const_heavy_programs(rng, P, d):
+    """Programs whose constant subexpressions the packing kernel folds: constants combined by
+    every operator kind (transcendentals, protected division and log, DUP, SWAP and DEL on
+    constants), mixed with inputs; some fold to invalid values (exp(100), 1e20 * 1e20)."""
+    C = S.CONST
+    pieces = [
+        [(C, 0.7), (S.SIN, 0)], [(C, 1.3), (C, -0.4), (S.PDIV, 0)], [(C, 2.0), (S.PLOG, 0)],
+        [(C, 0.3), (S.EXP, 0), (S.COS, 0)], [(C, -2.5), (S.PSQRT, 0), (S.SQUARE, 0)],
+        [(C, 0.2), (S.DUP, 0), (S.MUL, 0)], [(C, 1.5), (C, 0.25), (S.SWAP, 0), (S.SUB, 0)],
+        [(C, 3.0), (C, 9.0), (S.DEL, 0)], [(C, 0.5), (C, 0.0005), (S.PDIV, 0)],
+        [(C, 1.1), (C, 2.2), (S.POW, 0)], [(C, 0.9), (S.TANH, 0), (S.SIGN, 0), (S.CUBE, 0)],
+    ]
+    bad = [[(C, 100.0), (S.EXP, 0)], [(C, 1e20), (C, 1e20), (S.MUL, 0)]]
+    progs = []
+    for i in range(P):
+        toks = [(S.LOAD0 + int(rng.integers(d)), 0.0)]
+        for _ in range(int(rng.integers(1, 6))):
+            piece = bad[int(rng.integers(2))] if rng.random() < 0.05 else \
+                pieces[int(rng.integers(len(pieces)))]
+            toks += piece + [(int(rng.choice([S.ADD, S.SUB, S.MUL, S.PDIV])), 0.0)]
+            if rng.random() < 0.4:
+                toks += [(S.LOAD0 + int(rng.integers(d)), 0.0), (S.MUL, 0.0)]
+        progs.append(toks)
+    return S.from_token_lists(progs)
+
+
+def test_constant_folding_same_bits_and_oracle():
+    """Constant subexpressions folded by the packing kernel: every program gives the bits it
+    gives when each work item packs it unfolded (programs in the caller's order), on the
+    scores and on every case's output, and agrees with the oracle."""
+    rng = np.random.default_rng(77)
+    d, N = 3, 1300
+    X = rng.uniform(-2, 2, (d, N)).astype(np.float32)
+    y = (X[0] * X[1] + np.cos(X[2])).astype(np.float32)
+    progs = _const_heavy_programs(rng, 600, d)
+    refs = parity.references(progs, X, y)
+    ds = beagle.Dataset(X, y)
+    dp = beagle.DevicePrograms(progs)
+    try:
+        folded = beagle.unpack_fitness(beagle.score_programs(dp, ds))
+        fout, _ = beagle.eval_programs(dp, ds)
+        fout = fout.cpu().numpy()
+        beagle.set_launch_config(keep_order=1)
+        plain = beagle.unpack_fitness(beagle.score_programs(dp, ds))
+        pout, _ = beagle.eval_programs(dp, ds)
+        pout = pout.cpu().numpy()
+    finally:
+        beagle.reset_launch_config()
+    for a, b in zip(folded, plain):
+        assert np.array_equal(a, b, equal_nan=True)
+    assert np.array_equal(fout, pout, equal_nan=True)
+    assert np.any(folded[2] & beagle.FLAG_INVALID) and not np.all(folded[2] & beagle.FLAG_INVALID)
+    parity.check_fp32(folded, refs)
+    ds.release()
