@@ -380,11 +380,13 @@ beagle_status beagle_serve_destroy(beagle_server *server);
 /*
  * Launch shape of the scoring kernel (no counterpart in the paper). All fields 0 = chosen
  * automatically. cases_per_lane: fitness cases each lane evaluates per pass on the FP32 path
- * (2, 4 or 8); tile: cases per staged tile (256 or 512; 8 cases per lane always uses 256);
- * group: programs per work item;
+ * (2, 4 or 8); tile: cases per staged tile (256 or 512); group: programs per work item;
  * warps: upper bound on consumer warps per CTA (1-31); grid: CTAs (default one per SM);
- * keep_order: 1 processes programs in the caller's order, 0 in the length-bucketed order
- * (longest first) where the planner chooses it.
+ * keep_order: 0 automatic -- on launches of at least 2^24 program-cases (P x N summed) the
+ * programs run in the length-bucketed order (longest first), each packed once for the call
+ * by a packing kernel that also folds their constant subexpressions (FP32 path); smaller
+ * launches keep the caller's order and pack per work item; 1 always the caller's order (no
+ * packing kernel); 2 always the length-bucketed order with the packing kernel.
  * beagle_set_launch_config sets the process-wide configuration used by every later scoring
  * call (NULL restores automatic); results do not depend on it beyond the rounding of sums
  * over differently sized tiles (tile) -- with a fixed tile they are bit-identical.

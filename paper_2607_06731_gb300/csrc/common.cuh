@@ -96,7 +96,6 @@ struct JobDev {
     uint2 *packed;
     const uint32_t *poff;
     uint32_t *pmeta;
-    int64_t fold_base;       // this job's slice of the launch's folded-program scratch
 };
 
 // Packer result of a pre-packed program: bits 0-15 the handler count, then the flags.

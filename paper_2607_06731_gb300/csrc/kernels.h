@@ -45,22 +45,28 @@ cudaError_t launch_score(const LaunchParams<1> &prm, int precision, int cases, i
 // Where poff[j] is set, the same kernel gives each position of the order its offset in a
 // packed-token buffer of pcap[j] tokens (each program its length + 1 tokens, in order; those
 // that do not fit, and lengths outside [1, kMaxLen], get kPackNone).
+// The sort runs over chunks of kOrderChunk programs: job j's chunks are chunk0[j] onward
+// (nchunks over all jobs); hist holds nchunks x (kMaxLen + 2) counts and totals njobs x
+// (kMaxLen + 2) counts, zeroed before the launch.
+constexpr int64_t kOrderChunk = 4096;
 struct OrderParams {
     const int32_t *lens[kMaxJobs];
     int32_t *order[kMaxJobs];
     uint32_t *poff[kMaxJobs];
     int64_t pcap[kMaxJobs];
     int64_t P[kMaxJobs];
+    int64_t chunk0[kMaxJobs];
+    int32_t *hist;
+    int32_t *totals;
+    int64_t nchunks;
     int32_t njobs;
 };
 cudaError_t launch_length_order(const OrderParams &prm, cudaStream_t s);
 // Pack every program of the jobs that carry a packed-token buffer (JobDev::packed), once per
 // call, for the fast pass's 16-value stack; programs deeper than that go to the deep lists.
-// On the FP32 path constant subexpressions are folded first, into fold_ops / fold_cs (as many
-// entries as the jobs' packed buffers, job j's from JobDev::fold_base), unless they are null.
+// On the FP32 path constant subexpressions are folded first.
 template <int MAXJ>
-cudaError_t launch_pack(const LaunchParams<MAXJ> &prm, int precision, uint8_t *fold_ops,
-                        float *fold_cs, cudaStream_t s);
+cudaError_t launch_pack(const LaunchParams<MAXJ> &prm, int precision, cudaStream_t s);
 
 // Opt-in CUDA-event timing of scoring-kernel launches (beagle_kernel_timing).
 bool timing_enabled();

@@ -77,23 +77,31 @@ beagle_status enqueue(const std::vector<Planned> &jobs, size_t b, size_t e, int 
         const int64_t c = P * kPackedPerProgram;
         return c < int64_t(0xfffffffe) ? c : int64_t(0xfffffffe);
     };
-    int64_t fold_entries = 0;   // folded-program scratch (FP32): one entry per packed token
     for (size_t i = b; i < e; ++i) {
         scratch += up256(jobs[i].part_bytes) + up256(sizeof(int32_t) * jobs[i].dev.P);
         if (sort && !jobs[i].dev.order) {
             scratch += up256(sizeof(int32_t) * jobs[i].dev.P) +
                        up256(sizeof(uint2) * pack_cap(jobs[i].dev.P)) +
                        2 * up256(sizeof(uint32_t) * jobs[i].dev.P);
-            fold_entries += pack_cap(jobs[i].dev.P);
         }
     }
-    if (precision != BEAGLE_FP32_COMPENSATED) fold_entries = 0;
-    scratch += up256(sizeof(float) * fold_entries) + up256(fold_entries);
+    // the length sort's counts: per-chunk histograms and per-job bucket totals (zeroed with the
+    // header)
+    int64_t nchunks = 0;
+    int norder = 0;
+    for (size_t i = b; i < e; ++i)
+        if (sort && !jobs[i].dev.order) {
+            nchunks += (jobs[i].dev.P + kOrderChunk - 1) / kOrderChunk;
+            ++norder;
+        }
+    const size_t totals_bytes = up256(sizeof(int32_t) * (kMaxLen + 2) * norder);
+    const size_t hist_bytes = up256(sizeof(int32_t) * (kMaxLen + 2) * nchunks);
+    scratch += totals_bytes + hist_bytes;
     char *base = nullptr;
     cudaError_t err = cudaMallocAsync(reinterpret_cast<void **>(&base), scratch, s);
     if (err != cudaSuccess)
         return fail(BEAGLE_ERR_OOM, "scratch of %zu bytes: %s", scratch, cudaGetErrorString(err));
-    err = cudaMemsetAsync(base, 0, kHdrBytes, s);
+    err = cudaMemsetAsync(base, 0, kHdrBytes + totals_bytes, s);
     if (err != cudaSuccess) {
         cudaFreeAsync(base, s);
         return cuda_fail(err, "scratch memset");
@@ -101,11 +109,10 @@ beagle_status enqueue(const std::vector<Planned> &jobs, size_t b, size_t e, int 
     prm.counter = reinterpret_cast<unsigned int *>(base + kHdrCounter);
     prm.error = reinterpret_cast<unsigned int *>(base + kHdrError);
     char *cur = base + kHdrBytes;
-    float *fold_cs = fold_entries ? reinterpret_cast<float *>(cur) : nullptr;
-    cur += up256(sizeof(float) * fold_entries);
-    uint8_t *fold_ops = fold_entries ? reinterpret_cast<uint8_t *>(cur) : nullptr;
-    cur += up256(fold_entries);
-    int64_t fold_next = 0;
+    int32_t *order_totals = reinterpret_cast<int32_t *>(cur);
+    cur += totals_bytes;
+    int32_t *order_hist = reinterpret_cast<int32_t *>(cur);
+    cur += hist_bytes;
     int64_t items = 0;
     int nj = 0;
     OrderParams op;
@@ -131,13 +138,13 @@ beagle_status enqueue(const std::vector<Planned> &jobs, size_t b, size_t e, int 
             prm.jobs[nj].packed = packed;
             prm.jobs[nj].poff = poff;
             prm.jobs[nj].pmeta = pmeta;
-            prm.jobs[nj].fold_base = fold_next;
-            fold_next += pack_cap(jobs[i].dev.P);
             op.lens[op.njobs] = jobs[i].dev.lens;
             op.order[op.njobs] = ord;
             op.poff[op.njobs] = poff;
             op.pcap[op.njobs] = pack_cap(jobs[i].dev.P);
             op.P[op.njobs] = jobs[i].dev.P;
+            op.chunk0[op.njobs] = op.nchunks;
+            op.nchunks += (jobs[i].dev.P + kOrderChunk - 1) / kOrderChunk;
             ++op.njobs;
         }
         prm.jobs[nj].groups = static_cast<int32_t>((jobs[i].dev.P + group - 1) / group);
@@ -150,8 +157,10 @@ beagle_status enqueue(const std::vector<Planned> &jobs, size_t b, size_t e, int 
     prm.group = group;
     prm.xbuf_floats = xbuf_floats;
     apply_wait_settings(&prm.wait_limit_ns, &prm.stall_producer);
+    op.hist = order_hist;
+    op.totals = order_totals;
     cudaError_t le = launch_length_order(op, s);
-    if (le == cudaSuccess) le = launch_pack(prm, precision, fold_ops, fold_cs, s);
+    if (le == cudaSuccess) le = launch_pack(prm, precision, s);
     if (le == cudaSuccess) {
         if constexpr (MAXJ == 1) le = launch_score(prm, precision, cases, nw, grid, s);
         else le = launch_score_batch(prm, precision, cases, nw, grid, s);
@@ -275,7 +284,12 @@ beagle_status score_jobs(const JobRequest *reqs, int n, int precision, cudaStrea
         }
         int group = plan_group(work, nw, grid);
         if (cfg.group) group = cfg.group;
-        const bool sort = !cfg.unsorted;
+        // The length order and the packing kernel (programs packed and folded once per call)
+        // pay for their launches only on launches of some size: smaller ones keep the caller's
+        // order and pack per work item.
+        int64_t pcases = 0;
+        for (const Planned &pj : lj) pcases += pj.dev.P * pj.dev.N;
+        const bool sort = cfg.unsorted == 2 || (cfg.unsorted == 0 && pcases >= kLaunchCases);
         if (lj.size() == 1)
             return enqueue<1>(lj, 0, 1, precision, cases, tile, group, nw, grid, xbuf_floats,
                               sort, s);
@@ -364,12 +378,14 @@ extern "C" beagle_status beagle_set_launch_config(const beagle_launch_config *cf
             return beagle::fail(BEAGLE_ERR_ARG, "tile must be 0, 256 or 512");
         if (cfg->warps < 0 || cfg->warps > 31 || cfg->group < 0 || cfg->grid < 0)
             return beagle::fail(BEAGLE_ERR_ARG, "bad launch configuration");
+        if (cfg->keep_order < 0 || cfg->keep_order > 2)
+            return beagle::fail(BEAGLE_ERR_ARG, "keep_order must be 0, 1 or 2");
         t.cases = cfg->cases_per_lane;
         t.tile = cfg->tile;
         t.group = cfg->group;
         t.warps = cfg->warps;
         t.grid = cfg->grid;
-        t.unsorted = cfg->keep_order ? 1 : 0;
+        t.unsorted = cfg->keep_order;
     }
     beagle::set_tune(t);
     return BEAGLE_OK;

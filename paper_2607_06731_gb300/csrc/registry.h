@@ -56,7 +56,7 @@ struct Tune {
     int grid = 0;    // CTAs
     int warps = 0;   // consumer warps per CTA (upper bound)
     int cases = 0;   // fitness cases per lane, FP32 path (2, 4, 8)
-    int unsorted = 0;  // 1: keep the caller's program order (no length-bucketed order)
+    int unsorted = 0;  // 0 automatic, 1 the caller's program order, 2 always the length order
     bool is_auto() const { return !group && !tile && !grid && !warps && !cases && !unsorted; }
 };
 

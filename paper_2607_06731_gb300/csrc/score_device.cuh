@@ -689,73 +689,133 @@ __device__ __forceinline__ double word_pair(const uint32_t *w0, const uint32_t *
     }
 }
 
+// Sums over a group of g lanes (g a power of two, the group aligned), the same butterfly on
+// every lane of the group: each level adds two values that commute, so every lane ends with
+// the same bits, and the tree, hence the bits, depends only on g and on the lane each value
+// started on.
+__device__ __forceinline__ double group_sum_f64(double v, int g) {
+    for (int o = g >> 1; o >= 1; o >>= 1) v += __shfl_xor_sync(kFull, v, o, g);
+    return v;
+}
+__device__ __forceinline__ float group_sum_f32(float v, int g) {
+    for (int o = g >> 1; o >= 1; o >>= 1) v += __shfl_xor_sync(kFull, v, o, g);
+    return v;
+}
+// Lanes that merge one program's tiles: a power of two, at most 32 and at most the tile count
+// rounded up (this GPU's fp64 rate is low: a warp's fp64 add takes 16 cycles, so few tiles are
+// merged by few lanes).
+__host__ __device__ __forceinline__ int finalize_group(int tiles) {
+    int g = 1;
+    while (g < 32 && g < tiles) g <<= 1;
+    return g;
+}
+
 // One program's MSE and 1 - r^2 from its tile partials (tile: cases per tile; timed_out: the
-// launch's error word was set).
+// launch's error word was set), by a group of g = finalize_group(tiles) lanes of a warp (all 32
+// lanes call it; r = lane % g): lane r takes tiles r, r + g, ..., then group sums. Two passes: the flags, sum of squared errors and output sum, then the sums centred on
+// the program's mean. On the FP32 path each tile sum is a compensated pair (s, c): the s parts
+// are added in fp64, the small c parts (about 2^-24 |s| each) in fp32, whose rounding adds
+// about 2^-48 of the sum; an exponent k != 0 marks a tile whose terms were scaled by 2^-k.
+// Few fp64 operations per tile: this GPU's fp64 rate is low. Lane 0 writes the result.
 template <bool FP64>
 __device__ __forceinline__ void finalize_mse_program(const JobDev &J, int64_t p, int tile,
-                                                     bool timed_out) {
+                                                     bool timed_out, int lane) {
     const int T = J.tiles;
+    const int g = finalize_group(T);
+    const int rl = lane & (g - 1);
     const int64_t P = J.P;
     auto W = [&](int f, int t) { return J.partials + (static_cast<int64_t>(f) * T + t) * P + p; };
     beagle_fitness r;
     r.reserved = 0u;
     const double inf = __longlong_as_double(0x7ff0000000000000ll);
-    uint32_t flags = 0u;
     if (timed_out) {
         r.mse = r.one_minus_r2 = __longlong_as_double(0x7ff8000000000000ll);
         r.flags = BEAGLE_FLAG_TIMEOUT;
-        J.out[p] = r;
+        if (rl == 0) J.out[p] = r;
         return;
     }
+    auto mean_of = [&](int t) {
+        return FP64 ? word_pair<true>(W(kMean, t), W(kMean64, t))
+                    : static_cast<double>(__uint_as_float(*W(kMean, t)));
+    };
+    const double m0 = mean_of(0);
+    uint32_t flags = 0u;
     bool nonconst = false, mdiff = false;
-    double sse = 0.0, sumf = 0.0, m0 = 0.0;
-    for (int t = 0; t < T; ++t) {
+    double sse = 0.0, sumf = 0.0;
+    float sse_c = 0.0f, sumf_c = 0.0f;
+    for (int t = rl; t < T; t += g) {
         const uint32_t tf = *W(kTileFlags, t);
         if (tf & TF_MALFORMED) flags |= BEAGLE_FLAG_MALFORMED;
         if (tf & TF_INVALID) flags |= BEAGLE_FLAG_INVALID;
+        if (flags) continue;
+        const double n = static_cast<double>(min(static_cast<int64_t>(tile),
+                                                 J.N - static_cast<int64_t>(t) * tile));
+        const double m = mean_of(t);
+        const int ke = (tf >> 8) & 0xff, kd = (tf >> 16) & 0xff;
+        if (FP64 || ke != 0) {
+            sse += ldexp(word_pair<FP64>(W(kSe2, t), W(kSe2 + 1, t)), 2 * ke);
+        } else {
+            sse += static_cast<double>(__uint_as_float(*W(kSe2, t)));
+            sse_c += __uint_as_float(*W(kSe2 + 1, t));
+        }
+        if (FP64 || kd != 0) {
+            sumf += n * m + ldexp(word_pair<FP64>(W(kSd, t), W(kSd + 1, t)), kd);
+        } else {
+            sumf += n * m + static_cast<double>(__uint_as_float(*W(kSd, t)));
+            sumf_c += __uint_as_float(*W(kSd + 1, t));
+        }
+        nonconst |= (tf & TF_NONCONST) != 0u;
+        mdiff |= (m != m0);
+    }
+    for (int o = g >> 1; o >= 1; o >>= 1) {
+        flags |= __shfl_xor_sync(kFull, flags, o, g);
+        nonconst |= __shfl_xor_sync(kFull, nonconst ? 1 : 0, o, g) != 0;
+        mdiff |= __shfl_xor_sync(kFull, mdiff ? 1 : 0, o, g) != 0;
     }
     if (flags) {
         r.mse = r.one_minus_r2 = inf;
         r.flags = flags;
-        J.out[p] = r;
+        if (rl == 0) J.out[p] = r;
         return;
     }
-    for (int t = 0; t < T; ++t) {
-        const double n = static_cast<double>(min(static_cast<int64_t>(tile),
-                                                 J.N - static_cast<int64_t>(t) * tile));
-        const double m = FP64 ? word_pair<true>(W(kMean, t), W(kMean64, t))
-                              : static_cast<double>(__uint_as_float(*W(kMean, t)));
-        const uint32_t tf = *W(kTileFlags, t);
-        const int ke = (tf >> 8) & 0xff, kd = (tf >> 16) & 0xff;
-        sse += ldexp(word_pair<FP64>(W(kSe2, t), W(kSe2 + 1, t)), 2 * ke);
-        sumf += n * m + ldexp(word_pair<FP64>(W(kSd, t), W(kSd + 1, t)), kd);
-        nonconst |= (tf & TF_NONCONST) != 0u;
-        if (t == 0) m0 = m;
-        else mdiff |= (m != m0);
-    }
+    sse = group_sum_f64(sse, g) + static_cast<double>(group_sum_f32(sse_c, g));
+    sumf = group_sum_f64(sumf, g) + static_cast<double>(group_sum_f32(sumf_c, g));
     const double N = static_cast<double>(J.N);
     r.mse = sse / N;
     if (!nonconst && !mdiff) {
         r.one_minus_r2 = 1.0;
         r.flags = BEAGLE_FLAG_DEGENERATE;
-        J.out[p] = r;
+        if (rl == 0) J.out[p] = r;
         return;
     }
     const double fbar = sumf / N;
     double sff = 0.0, sfy = 0.0;
-    for (int t = 0; t < T; ++t) {
+    float sff_c = 0.0f, sfy_c = 0.0f;
+    for (int t = rl; t < T; t += g) {
         const double n = static_cast<double>(min(static_cast<int64_t>(tile),
                                                  J.N - static_cast<int64_t>(t) * tile));
-        const double m = FP64 ? word_pair<true>(W(kMean, t), W(kMean64, t))
-                              : static_cast<double>(__uint_as_float(*W(kMean, t)));
+        const double m = mean_of(t);
         const uint32_t tf = *W(kTileFlags, t);
         const int kd = (tf >> 16) & 0xff, ky = (tf >> 24) & 0xff;
         const double dm = m - fbar;
-        const double sd = ldexp(word_pair<FP64>(W(kSd, t), W(kSd + 1, t)), kd);
-        sff += ldexp(word_pair<FP64>(W(kSdd, t), W(kSdd + 1, t)), 2 * kd) + 2.0 * dm * sd +
-               n * dm * dm;
-        sfy += ldexp(word_pair<FP64>(W(kSdy, t), W(kSdy + 1, t)), kd + ky) + dm * J.tile_sy[t];
+        double sd, sdd, sdy;
+        if (FP64 || (kd | ky) != 0) {
+            sd = ldexp(word_pair<FP64>(W(kSd, t), W(kSd + 1, t)), kd);
+            sdd = ldexp(word_pair<FP64>(W(kSdd, t), W(kSdd + 1, t)), 2 * kd);
+            sdy = ldexp(word_pair<FP64>(W(kSdy, t), W(kSdy + 1, t)), kd + ky);
+        } else {
+            sd = static_cast<double>(__uint_as_float(*W(kSd, t)));
+            sdd = static_cast<double>(__uint_as_float(*W(kSdd, t)));
+            sdy = static_cast<double>(__uint_as_float(*W(kSdy, t)));
+            sff_c += __uint_as_float(*W(kSdd + 1, t)) +
+                     2.0f * static_cast<float>(dm) * __uint_as_float(*W(kSd + 1, t));
+            sfy_c += __uint_as_float(*W(kSdy + 1, t));
+        }
+        sff += sdd + 2.0 * dm * sd + n * dm * dm;
+        sfy += sdy + dm * J.tile_sy[t];
     }
+    sff = group_sum_f64(sff, g) + static_cast<double>(group_sum_f32(sff_c, g));
+    sfy = group_sum_f64(sfy, g) + static_cast<double>(group_sum_f32(sfy_c, g));
     if (!(sff > 0.0)) {
         r.one_minus_r2 = 1.0;
         r.flags = BEAGLE_FLAG_DEGENERATE;
@@ -764,7 +824,7 @@ __device__ __forceinline__ void finalize_mse_program(const JobDev &J, int64_t p,
         r.one_minus_r2 = 1.0 - rr * rr;
         r.flags = 0u;
     }
-    J.out[p] = r;
+    if (rl == 0) J.out[p] = r;
 }
 
 

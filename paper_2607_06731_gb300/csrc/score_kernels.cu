@@ -177,15 +177,21 @@ score_kernel(const __grid_constant__ LaunchParams<MAXJ> prm) {
     }
 }
 
+// A group of finalize_group(tiles) lanes per program; blockIdx.x counts blocks of 256 groups'
+// lanes (256 / g programs a block).
 template <bool FP64, int MAXJ>
 __global__ void finalize_kernel(const __grid_constant__ LaunchParams<MAXJ> prm) {
     const int jn = blockIdx.y;
     if (jn >= prm.njobs) return;
     const JobDev &J = prm.jobs[jn];
     if (J.kind != kFitMse) return;
-    const int64_t p = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (p >= J.P) return;
-    finalize_mse_program<FP64>(J, p, prm.tile, *prm.error != 0u);
+    const int g = finalize_group(J.tiles);
+    const int64_t p = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) / g;
+    // whole warps leave together (the group sums shuffle over the warp)
+    const int64_t pw = (static_cast<int64_t>(blockIdx.x) * blockDim.x + (threadIdx.x & ~31)) / g;
+    if (pw >= J.P) return;
+    finalize_mse_program<FP64>(J, p < J.P ? p : J.P - 1, prm.tile, *prm.error != 0u,
+                               threadIdx.x & 31);
 }
 
 template <bool FP64, int MAXJ>
@@ -253,8 +259,11 @@ static cudaError_t launch_impl(const LaunchParams<MAXJ> &prm, int nw, int grid,
     if (maxP > 0) {
         dim3 fg(static_cast<unsigned>((maxP + 255) / 256), static_cast<unsigned>(prm.njobs));
         if (mse) {
-            if (sizeof(T) == 8) finalize_kernel<true, MAXJ><<<fg, 256, 0, stream>>>(prm);
-            else finalize_kernel<false, MAXJ><<<fg, 256, 0, stream>>>(prm);
+            int gmax = 1;
+            for (int j = 0; j < prm.njobs; ++j) gmax = max(gmax, finalize_group(prm.jobs[j].tiles));
+            const dim3 fw(static_cast<unsigned>((maxP * gmax + 255) / 256), static_cast<unsigned>(prm.njobs));
+            if (sizeof(T) == 8) finalize_kernel<true, MAXJ><<<fw, 256, 0, stream>>>(prm);
+            else finalize_kernel<false, MAXJ><<<fw, 256, 0, stream>>>(prm);
             e = cudaGetLastError();
         }
         if (fit && e == cudaSuccess) {
@@ -338,11 +347,11 @@ cudaError_t launch_deep_and_finalize(const LaunchParams<1> &prm, int precision, 
     if (precision == BEAGLE_FP64) {
         const int nw = fit_warps<double, kCasesFp64, kMaxDepth>(prm.xbuf_floats, prm.tile, 0);
         e = launch_pass<double, kCasesFp64, kMaxDepth, 1>(dp, nw, sm_count_dev(), s);
-        if (e == cudaSuccess) finalize_kernel<true, 1><<<dim3(static_cast<unsigned>((prm.jobs[0].P + 255) / 256), 1), 256, 0, s>>>(prm);
+        if (e == cudaSuccess) finalize_kernel<true, 1><<<dim3(static_cast<unsigned>((prm.jobs[0].P * finalize_group(prm.jobs[0].tiles) + 255) / 256), 1), 256, 0, s>>>(prm);
     } else {
         const int nw = fit_warps<float, 4, kMaxDepth>(prm.xbuf_floats, prm.tile, 0);
         e = launch_pass<float, 4, kMaxDepth, 1>(dp, nw, sm_count_dev(), s);
-        if (e == cudaSuccess) finalize_kernel<false, 1><<<dim3(static_cast<unsigned>((prm.jobs[0].P + 255) / 256), 1), 256, 0, s>>>(prm);
+        if (e == cudaSuccess) finalize_kernel<false, 1><<<dim3(static_cast<unsigned>((prm.jobs[0].P * finalize_group(prm.jobs[0].tiles) + 255) / 256), 1), 256, 0, s>>>(prm);
     }
     return e == cudaSuccess ? cudaGetLastError() : e;
 }

@@ -177,13 +177,20 @@ serve_kernel(const __grid_constant__ ServeParams prm) {
             const int64_t p = J.order ? static_cast<int64_t>(J.order[q]) : q;
             const int deep = process_program<T, K, D>(J, q, p, s.tile, tile, xs, pbuf, fbuf, stk,
                                                       tstk, lane);
+            // count the unit; the warp that completes the program's last tile merges them
+            int last = 0;
             if (lane == 0) {
                 __threadfence();   // this unit's partials before its count
                 const int prev = atomicAdd(&SJ.tile_done[p], 1);
-                if (!deep && prev == J.tiles - 1) {
-                    __threadfence();
-                    finalize_mse_program<sizeof(T) == 8>(J, p, tile, false);
-                }
+                last = (!deep && prev == J.tiles - 1) ? 1 : 0;
+                if (last) __threadfence();
+            }
+            if (__shfl_sync(kFull, last, 0)) {
+                __syncwarp();
+                finalize_mse_program<sizeof(T) == 8>(J, p, tile, false, lane);
+                __syncwarp();
+            }
+            if (lane == 0) {
                 __threadfence();
                 if (atomicAdd(&SJ.counters[0], 1ull) == units - 1) {
                     ServeDone *dn = SJ.done;

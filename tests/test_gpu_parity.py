@@ -491,10 +491,11 @@ def test_constant_folding_same_bits_and_oracle():
     ds = beagle.Dataset(X, y)
     dp = beagle.DevicePrograms(progs)
     try:
+        beagle.set_launch_config(keep_order=2)   # the packing kernel (it folds)
         folded = beagle.unpack_fitness(beagle.score_programs(dp, ds))
         fout, _ = beagle.eval_programs(dp, ds)
         fout = fout.cpu().numpy()
-        beagle.set_launch_config(keep_order=1)
+        beagle.set_launch_config(keep_order=1)   # each work item packs, unfolded
         plain = beagle.unpack_fitness(beagle.score_programs(dp, ds))
         pout, _ = beagle.eval_programs(dp, ds)
         pout = pout.cpu().numpy()
@@ -505,4 +506,38 @@ def test_constant_folding_same_bits_and_oracle():
     assert np.array_equal(fout, pout, equal_nan=True)
     assert np.any(folded[2] & beagle.FLAG_INVALID) and not np.all(folded[2] & beagle.FLAG_INVALID)
     parity.check_fp32(folded, refs)
+    ds.release()
+
+
+@pytest.mark.parametrize("cases", [4, 8, 2])
+def test_packing_kernel_same_bits_as_per_item_packing(cases):
+    """Programs packed once per call by the packing kernel (length order, constant folding,
+    the deep list filled by the packing kernel) give the bits of programs each work item packs
+    itself: random programs of every operator, deep ones, register (COPY/PASTE) ones,
+    constant-heavy ones, and malformed ones (flagged the same way)."""
+    rng = np.random.default_rng(90 + cases)
+    d, N = 3, 1500
+    X = rng.uniform(-1.5, 1.5, (d, N)).astype(np.float32)
+    y = (X[0] * X[1] - np.tanh(X[2])).astype(np.float32)
+    parts = [S.gen_programs(rng, 300, 4, 90, d, unary=S.ALL_UNARY, binary=S.ALL_BINARY),
+             _deep_population(rng, 200, d)[0], _const_heavy_programs(rng, 200, d),
+             S.with_registers(S.gen_programs(rng, 200, 6, 60, d), 5, 0.5, 4)]
+    C = S.CONST
+    bad = S.from_token_lists([[(S.ADD, 0)], [(C, 1.0), (C, 2.0)], [(S.LOAD0 + 5, 0)],
+                              [(C, 1.0)] * 33 + [(S.ADD, 0)] * 32,
+                              [(C, 1.0), (C, 2.0), (S.ADD, 0), (S.ADD, 0)]])
+    toks = [t for pr in parts + [bad] for t in (pr.program(p) for p in range(pr.P))]
+    progs = S.from_token_lists([list(zip(o, c)) for o, c in toks])
+    ds = beagle.Dataset(X, y)
+    dp = beagle.DevicePrograms(progs)
+    got = {}
+    try:
+        for mode in (1, 2):
+            beagle.set_launch_config(cases_per_lane=cases, keep_order=mode)
+            got[mode] = beagle.unpack_fitness(beagle.score_programs(dp, ds))
+    finally:
+        beagle.reset_launch_config()
+    for a, b in zip(got[1], got[2]):
+        assert np.array_equal(a, b, equal_nan=True)
+    assert np.all(got[2][2][-5:] & beagle.FLAG_MALFORMED)
     ds.release()
