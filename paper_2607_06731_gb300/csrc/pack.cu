@@ -19,7 +19,8 @@ namespace {
 // value that fails the validity rule makes the program invalid, as it would on every case.
 // FP32 path only: a folded double could not travel in the program's fp32 constants.
 // Programs using DUP, SWAP, DEL or the COPY / PASTE registers are not folded.
-__device__ __forceinline__ float fold_unary(int op, float a) {
+// Out of line: the folds are few, the code of these functions large.
+static __device__ __noinline__ float fold_unary(int op, float a) {
     using A = Arith<float>;
     switch (op) {
     case OP_SIN: return A::sin_(a);
@@ -39,7 +40,7 @@ __device__ __forceinline__ float fold_unary(int op, float a) {
     }
 }
 
-__device__ __forceinline__ float fold_binary(int op, float a, float b) {   // a op b, b the top
+static __device__ __noinline__ float fold_binary(int op, float a, float b) {   // a op b, b the top
     using A = Arith<float>;
     switch (op) {
     case OP_ADD: return __fadd_rn(a, b);
@@ -101,16 +102,16 @@ __device__ int warp_fold(FoldBuf &fb, int n, int d, int lane, bool *bad) {
     }
     if (!__all_sync(kFull, ok) || depth != 1) return -1;
     bool any_fold = false, b = false;
-    for (int pass = 0; pass < 32; ++pass) {
-        // decisions (reads only), then the rewrite with compaction
-        for (int base = 0; base < n; base += 32) {
-            const int j = base + lane;
-            if (j < n) {
-                fb.kill[j] = 0;
-                fb.set[j] = 0;
-            }
+    for (int base = 0; base < n; base += 32) {
+        const int j = base + lane;
+        if (j < n) {
+            fb.kill[j] = 0;
+            fb.set[j] = 0;
         }
-        __syncwarp();
+    }
+    __syncwarp();
+    for (int pass = 0; pass < 32; ++pass) {
+        // decisions (reads only), then the rewrite with compaction (which clears the flags)
         bool folded = false;
         for (int base = 0; base < n; base += 32) {
             const int j = base + lane;
@@ -152,6 +153,10 @@ __device__ int warp_fold(FoldBuf &fb, int n, int d, int lane, bool *bad) {
             const float c = in ? (fb.set[j] ? fb.nv[j] : fb.cs[j]) : 0.0f;
             const unsigned m = __ballot_sync(kFull, keep);
             __syncwarp();
+            if (in) {
+                fb.kill[j] = 0;
+                fb.set[j] = 0;
+            }
             if (keep) {
                 const int pos = out + __popc(m & ((1u << lane) - 1u));
                 fb.ops[pos] = op;
