@@ -269,9 +269,9 @@ def straight_line_peak(progs, N, rates):
 # The oracle (test infrastructure) runs only here, outside every timed region: the CPU
 # baseline, the reference arm, and the parity gates on a sample of the timed launch's output.
 def _oracle_worker(inp: str, outp: str):
-    """Spawned process: FP32-ops oracle results and FP64 oracle results with their running
-    error bound (the bound of a device computing in fp64 with its transcendentals' ulps) of a
-    program sample."""
+    """Spawned process: FP32-ops and FP64 oracle results of a program sample, each with its
+    running error bound (the bound of a device computing in that precision with its
+    transcendentals' ulps)."""
     sys.path.insert(0, ROOT)
     import oracle
     from paper_2607_06731_gb300 import synth
@@ -279,10 +279,10 @@ def _oracle_worker(inp: str, outp: str):
     z = np.load(inp)
     res = {}
     t0 = time.perf_counter()
-    m, r, f = oracle.score(z["ops"], z["offsets"], z["lengths"], z["consts"], z["X"], z["y"],
-                           "fp32")
-    res["fp32_mse"], res["fp32_omr2"], res["fp32_flags"] = m, r, f
     progs = synth.Programs(z["ops"], z["offsets"], z["lengths"], z["consts"])
+    m, r, f, bm, br = oracle.score_bound(progs, z["X"], z["y"], "fp32")
+    res["fp32_mse"], res["fp32_omr2"], res["fp32_flags"] = m, r, f
+    res["fp32_bm"], res["fp32_br"] = bm, br
     m, r, f, bm, br = oracle.score_bound(progs, z["X"], z["y"], "fp64")
     res["fp64_mse"], res["fp64_omr2"], res["fp64_flags"] = m, r, f
     res["fp64_bm"], res["fp64_br"] = bm, br
@@ -326,8 +326,9 @@ def oracle_inline(progs, X, y):
     import oracle
     oracle.build()
     res = {}
-    m, r, f = oracle.score(progs.ops, progs.offsets, progs.lengths, progs.consts, X, y, "fp32")
+    m, r, f, bm, br = oracle.score_bound(progs, X, y, "fp32")
     res["fp32_mse"], res["fp32_omr2"], res["fp32_flags"] = m, r, f
+    res["fp32_bm"], res["fp32_br"] = bm, br
     m, r, f, bm, br = oracle.score_bound(progs, X, y, "fp64")
     res["fp64_mse"], res["fp64_omr2"], res["fp64_flags"] = m, r, f
     res["fp64_bm"], res["fp64_br"] = bm, br
@@ -354,14 +355,15 @@ def parity_gates(g32, g64, o):
     """Gates A, B, C against the oracle. NEAR: the oracle saw a value within 1e-5 of a
     threshold (1e30, 1e-3), where fp32 and fp64 may decide differently; AMBIGUOUS: a decision
     lies inside the FP64 oracle's running error bound. The strict (well-conditioned) set for
-    the FP32 path: valid, neither, the FP32-ops and FP64 oracle results agree within 1e-6 (the
-    fitness moves by less than 1e-6 under fp32 rounding of every operation) and the FP64 error
-    bound is within 1e-9 (no chaotic sensitivity that the fp32 comparison could miss).
+    the FP32 path, as in the tests: valid, neither, the FP32-ops oracle's error bound within
+    1e-6 (a device whose fp32 transcendentals are within their ulp limits lands within 1e-6 of
+    the FP32-ops oracle), the FP32-ops and FP64 oracle results agree within 1e-6, and the FP64
+    error bound is within 1e-9 (no chaotic sensitivity that the fp32 comparison could miss).
       flags   GPU flags equal the oracle's on every program neither NEAR nor AMBIGUOUS
       gate A  GPU FP32c vs FP32-ops oracle, |g - o| <= max(1e-5 |o|, 1e-7), strict set
       gate B  GPU FP32c vs FP64 oracle, same tolerance, strict set
-      gate C  GPU FP64 vs FP64 oracle, |g - o| <= max(1e-12 |o|, 1e-13), on the strict
-              programs whose FP64 bound is within 1e-13 (as in the tests)"""
+      gate C  GPU FP64 vs FP64 oracle, |g - o| <= max(1e-12 |o|, 1e-13), on the valid,
+              decided programs whose FP64 bound is within 1e-13 (as in the tests)"""
     NEAR, AMBIG, BITS = 256, 512, 7
     f32, f64 = o["fp32_flags"].astype(np.int64), o["fp64_flags"].astype(np.int64)
     near = ((f32 | f64) & NEAR) != 0
@@ -373,8 +375,11 @@ def parity_gates(g32, g64, o):
     with np.errstate(invalid="ignore"):
         tight9 = (bm <= 1e-9 * np.abs(m64) + 1e-12) & (br <= 1e-9 * np.abs(r64) + 1e-12)
         tight13 = (bm <= 1e-13 * np.abs(m64) + 1e-15) & (br <= 1e-13 * np.abs(r64) + 1e-15)
-    strict = valid & ~near & ~amb & agree & tight9
-    strict_c = strict & tight13
+        m32, r32 = o["fp32_mse"], o["fp32_omr2"]
+        tight32 = ((o["fp32_bm"] <= 1e-6 * np.abs(m32) + 1e-9) &
+                   (o["fp32_br"] <= 1e-6 * np.abs(r32) + 1e-9))
+    strict = valid & ~near & ~amb & agree & tight9 & tight32
+    strict_c = valid & ~near & ~amb & tight13   # the FP64 path: its own bound decides
     decided = ~near & ~amb
     out = {"programs": int(len(f32)), "valid": int(valid.sum()), "near_threshold": int(near.sum()),
            "ambiguous": int(amb.sum()), "strict": int(strict.sum()),
