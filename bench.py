@@ -58,10 +58,12 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["headline", "c1", "c2", "c3", "c4", "c5"],
+    ap.add_argument("--workload", choices=["headline", "c1", "c2", "c3", "c4", "c5", "handlers"],
                     default="headline",
                     help="headline (default): the precision workload with oracle gates and "
-                         "compact c1/c2/c4 sub-lines; c1..c5: one workload on its own line")
+                         "compact c1/c2/c4 sub-lines; c1..c5: one workload on its own line; "
+                         "handlers: one scoring launch per interpreter handler (programs "
+                         "repeating it) for instruction counts under ncu")
     ap.add_argument("--fp64-steps", type=int, default=1)
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--parity-sample", type=int, default=10_000,
@@ -259,9 +261,10 @@ def roofline_line(node_evals, kernel_s, progs_list, sm_mhz, sms, peak_straight=N
 
 
 def straight_line_peak(progs, N, rates):
-    """Seconds straight-line compiled code would need for this op mix, every operator at its
-    measured throughput (beagle_measure_op_rates), leaves free."""
-    counts = np.bincount(progs.ops, minlength=256).astype(np.float64)
+    """Seconds straight-line compiled code would need for this op mix (the operators the
+    interpreter runs: folded constant subexpressions left out), every operator at its measured
+    throughput (beagle_measure_op_rates), leaves free."""
+    counts = np.bincount(progs.ops, minlength=256).astype(np.float64) - folded_op_counts(progs)
     return sum(counts[op] * N / r for op, r in rates.items())
 
 
@@ -947,11 +950,72 @@ def run_c5(args, beagle, synth, torch, clocks):
             "gpu_launches": sum(lv["launches"] for lv in levels.values()), "clocks": clk}
 
 
+# Programs that repeat one interpreter handler n times (after a first leaf), for the handler
+# profile: each (name, n) is one scoring launch of HANDLER_P programs on HANDLER_N cases.
+HANDLER_P, HANDLER_N = 2048, 1024
+
+
+def handler_programs():
+    from paper_2607_06731_gb300 import synth as S
+    L0, L1, C = S.LOAD0, S.LOAD0 + 1, S.CONST
+
+    def rep(body, n, suffix=()):
+        return [(L0, 0.0)] + list(body) * n + list(suffix)
+    return {
+        "ADDX": lambda n: rep([(L1, 0.0), (S.ADD, 0.0)], n),
+        "MULX": lambda n: rep([(L1, 0.0), (S.MUL, 0.0)], n),
+        "ADDC": lambda n: rep([(C, 0.5), (S.ADD, 0.0)], n),
+        "PDIVX": lambda n: rep([(L1, 0.0), (S.PDIV, 0.0)], n),
+        "PUSHX+ADD": lambda n: rep([(L1, 0.0)], n, [(S.ADD, 0.0)] * n),
+        "PUSHX+PDIV": lambda n: rep([(L1, 0.0)], n, [(S.PDIV, 0.0)] * n),
+        "DUP+MUL": lambda n: rep([(S.DUP, 0.0), (S.MUL, 0.0)], n),
+        "SIN": lambda n: rep([(S.SIN, 0.0)], n),
+        "COS": lambda n: rep([(S.COS, 0.0)], n),
+        "EXP": lambda n: rep([(S.EXP, 0.0)], n),
+        "PLOG": lambda n: rep([(S.PLOG, 0.0)], n),
+        "PSQRT": lambda n: rep([(S.PSQRT, 0.0)], n),
+        "SQUARE": lambda n: rep([(S.SQUARE, 0.0)], n),
+    }
+
+
+def run_handlers(args):
+    """One launch per (handler, n) for n = 8 and 15; prints each launch's interpreter steps
+    (tokens after leaf + binary fusion, plus END, per 128-case pass, over all programs). Under
+    ncu, (instructions(15) - instructions(8)) / (steps(15) - steps(8)) is the handler's cost."""
+    import torch
+    from paper_2607_06731_gb300 import beagle, synth as S
+    X = np.random.default_rng(0).uniform(0.5, 1.5, (3, HANDLER_N)).astype(np.float32)
+    y = (X[0] + X[1]).astype(np.float32)
+    ds = beagle.Dataset(X, y)
+    beagle.set_launch_config(cases_per_lane=4, tile=512, keep_order=1)
+    lines = []
+    try:
+        for name, mk in handler_programs().items():
+            for n in (8, 15):
+                toks = mk(n)
+                dp = beagle.DevicePrograms(S.from_token_lists([toks] * HANDLER_P))
+                beagle.score_programs(dp, ds)
+                torch.cuda.synchronize()
+                ops = [t[0] for t in toks]
+                leaf = [o == S.CONST or S.LOAD0 <= o < S.LOAD0 + 16 for o in ops]
+                fused = sum(1 for i in range(len(ops) - 1)
+                            if leaf[i] and ops[i + 1] in (S.ADD, S.SUB, S.MUL, S.PDIV))
+                steps = (len(ops) - fused + 1) * HANDLER_P * (HANDLER_N // 128)
+                lines.append({"handler": name, "n": n, "steps": steps})
+                print(json.dumps(lines[-1]), flush=True)
+    finally:
+        beagle.reset_launch_config()
+        ds.release()
+    return 0
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if args.workload == "handlers":
+        return run_handlers(args)
     if args.workload == "headline":
         return run_headline(args, rank, world, local)
     return run_single(args, rank, world, local)
