@@ -19,8 +19,7 @@ namespace {
 // value that fails the validity rule makes the program invalid, as it would on every case.
 // FP32 path only: a folded double could not travel in the program's fp32 constants.
 // Programs using DUP, SWAP, DEL or the COPY / PASTE registers are not folded.
-// Out of line: the folds are few, the code of these functions large.
-static __device__ __noinline__ float fold_unary(int op, float a) {
+__device__ __forceinline__ float fold_unary(int op, float a) {
     using A = Arith<float>;
     switch (op) {
     case OP_SIN: return A::sin_(a);
@@ -40,7 +39,7 @@ static __device__ __noinline__ float fold_unary(int op, float a) {
     }
 }
 
-static __device__ __noinline__ float fold_binary(int op, float a, float b) {   // a op b, b the top
+__device__ __forceinline__ float fold_binary(int op, float a, float b) {   // a op b, b the top
     using A = Arith<float>;
     switch (op) {
     case OP_ADD: return __fadd_rn(a, b);
