@@ -37,10 +37,15 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "GPoPs (node-evals/s) FP32-compensated vs plain FP64 at ≤1e-5 rel err; p50/p99"
-# kernels one scoring call launches: length order, packing (each program translated into
-# handlers once), the persistent scoring kernel's fast pass and deep pass (programs deeper
-# than 16 values; it exits at once when there are none), fp64 finalize
-LAUNCHES_PER_CALL = 5
+# Kernels one scoring call launches: on launches of at least 2^24 program-cases the length sort
+# (two kernels) and packing (each program translated into handlers once, constants folded),
+# then on every launch the persistent scoring kernel's fast pass and deep pass (programs deeper
+# than 16 values; it exits at once when there are none) and the fp64 finalize.
+PACKED_LAUNCH_CASES = 1 << 24
+
+
+def launches_per_call(P: int, N: int) -> int:
+    return 6 if P * N >= PACKED_LAUNCH_CASES else 3
 C1_DESC = ("c1-small-1024: P=1024 programs, length U{8..32}, d=2, N=1024 cases, X~U[-3,3], "
            "y = x0 sin(x1) + x0^2/2; MSE")
 C2_DESC = ("c2-population-100k: P=100000 programs, length U{16..128}, d=5, N=1024 cases, "
@@ -157,8 +162,8 @@ LANES_PER_SM_CLK = {"fp32": 128, "mufu": 32, "alu": 64, "issue": 128}
 def folded_op_counts(progs):
     """Per opcode, the operators the packing kernel folds (constant subexpressions, evaluated
     once per call instead of on every case): the constness of every stack value followed
-    through all programs at once, token position by token position. Programs that use the
-    COPY/PASTE registers are not folded (as on the device)."""
+    through all programs at once, token position by token position. As on the device, only
+    programs of leaves, unary and binary operators are folded."""
     from paper_2607_06731_gb300 import synth as S
     P = progs.P
     out = np.zeros(256, np.int64)
@@ -168,7 +173,7 @@ def folded_op_counts(progs):
     offs = progs.offsets.astype(np.int64)
     cst = np.zeros((P, 36), bool)
     sp = np.zeros(P, np.int64)
-    regs = np.zeros(P, bool)
+    other = np.zeros(P, bool)   # DUP, SWAP, DEL, COPY/PASTE or unknown: not folded
     per = []
     un = np.zeros(256, bool)
     for op in list(range(S.SIN, S.SQUARE + 1)) + list(range(S.POW + 1, S.TANH + 1)):
@@ -181,41 +186,55 @@ def folded_op_counts(progs):
         s_ = sp[act]
         isconst = op == S.CONST
         isvar = (op >= S.LOAD0) & (op < S.LOAD0 + 16)
-        regs[act[(op >= S.COPY0) & (op < S.PASTE0 + 16)]] = True
-        # leaves
+        u, b = un[op], bn[op]
+        other[act[~(isconst | isvar | u | b)]] = True
         lf = isconst | isvar
         cst[act[lf], np.minimum(s_[lf], 35)] = isconst[lf]
-        # unary: folded when the top is constant
-        u = un[op]
         fu = u & cst[act, np.maximum(s_ - 1, 0)]
-        # binary: folded when both operands are constant; the result is constant then
-        b = bn[op]
         both = cst[act, np.maximum(s_ - 1, 0)] & cst[act, np.maximum(s_ - 2, 0)]
         fb = b & both
         cst[act[b], np.maximum(s_[b] - 2, 0)] = both[b]
-        # DUP / SWAP / DEL on constants
-        dup = op == S.DUP
-        fd = dup & cst[act, np.maximum(s_ - 1, 0)]
-        cst[act[dup], np.minimum(s_[dup], 35)] = cst[act[dup], np.maximum(s_[dup] - 1, 0)]
-        sw = op == S.SWAP
-        fs = sw & both
-        a1 = cst[act[sw], np.maximum(s_[sw] - 1, 0)].copy()
-        cst[act[sw], np.maximum(s_[sw] - 1, 0)] = cst[act[sw], np.maximum(s_[sw] - 2, 0)]
-        cst[act[sw], np.maximum(s_[sw] - 2, 0)] = a1
-        dl = op == S.DEL
-        fdl = dl & cst[act, np.maximum(s_ - 1, 0)]
-        sp[act] += lf.astype(np.int64) + dup - b - dl
-        f = fu | fb | fd | fs | fdl
+        sp[act] += lf.astype(np.int64) - b
+        f = fu | fb
         per.append((act[f], op[f]))
     for idx, op in per:
-        keep = ~regs[idx]
+        keep = ~other[idx]
         np.add.at(out, op[keep], 1)
     return out
 
 
+def removed_tokens(folded):
+    """Tokens folding removes: one per folded unary operator (CONST U -> CONST), two per
+    folded binary one (CONST CONST B -> CONST)."""
+    from paper_2607_06731_gb300 import synth as S
+    bins = [S.ADD, S.SUB, S.MUL, S.PDIV, S.POW]
+    nb = int(folded[bins].sum())
+    return int(folded.sum()) + nb
+
+
+def launch_folds(P: int, N: int) -> bool:
+    """Whether a launch of this size runs the packing kernel (and so folds constants)."""
+    return P * N >= PACKED_LAUNCH_CASES
+
+
+def folding_info(progs, N):
+    """The config entry on constant folding: node evaluations of the original programs (the
+    metric's count) and of the programs the interpreter runs."""
+    ev = float(progs.lengths.sum(dtype=np.int64)) * N
+    if not launch_folds(progs.P, N):
+        return {"constant_folding": "off (launch below 2^24 program-cases)",
+                "executed_node_evals_per_step": ev}
+    rm = removed_tokens(folded_op_counts(progs))
+    return {"constant_folding": ("on: constant subexpressions evaluated once per call by the "
+                                 "packing kernel, same bits; value counts the original "
+                                 "programs' node evaluations"),
+            "executed_node_evals_per_step": ev - float(rm) * N,
+            "folded_token_fraction": rm / max(1.0, float(progs.lengths.sum(dtype=np.int64)))}
+
+
 def algorithmic_units(progs_list, folded=True):
     """Lane operations of each pipe over populations [(programs, N)], of the operators the
-    interpreter runs (the folded constant subexpressions left out unless folded=False)."""
+    interpreter runs (the folded constant subexpressions left out when folded)."""
     tot = {"fp32": 0.0, "mufu": 0.0, "alu": 0.0}
     for progs, N in progs_list:
         counts = np.bincount(progs.ops, minlength=256).astype(np.float64)
@@ -229,10 +248,10 @@ def algorithmic_units(progs_list, folded=True):
     return tot
 
 
-def roofline_time(progs_list, sm_mhz: float, sms: int):
+def roofline_time(progs_list, sm_mhz: float, sms: int, folded=True):
     """Roofline time of the populations' algorithmic work: the slowest of the FP32, MUFU and
     ALU pipes and of instruction issue, at the measured SM clock."""
-    units = algorithmic_units(progs_list)
+    units = algorithmic_units(progs_list, folded)
     f = sm_mhz * 1e6
     t = {k: units[k] / (LANES_PER_SM_CLK[k] * sms * f) for k in units}
     bind = max(t, key=t.get)
@@ -241,8 +260,9 @@ def roofline_time(progs_list, sm_mhz: float, sms: int):
                 float(p.lengths.sum(dtype=np.int64)) * N for p, N in progs_list))}
 
 
-def roofline_line(node_evals, kernel_s, progs_list, sm_mhz, sms, peak_straight=None):
-    rt = roofline_time(progs_list, sm_mhz, sms)
+def roofline_line(node_evals, kernel_s, progs_list, sm_mhz, sms, peak_straight=None,
+                  folded=True):
+    rt = roofline_time(progs_list, sm_mhz, sms, folded)
     peak = node_evals / rt["seconds"] / 1e9
     achieved = node_evals / kernel_s / 1e9 if kernel_s else None
     out = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "GPoPs",
@@ -260,11 +280,13 @@ def roofline_line(node_evals, kernel_s, progs_list, sm_mhz, sms, peak_straight=N
     return out
 
 
-def straight_line_peak(progs, N, rates):
+def straight_line_peak(progs, N, rates, folded=True):
     """Seconds straight-line compiled code would need for this op mix (the operators the
-    interpreter runs: folded constant subexpressions left out), every operator at its measured
-    throughput (beagle_measure_op_rates), leaves free."""
-    counts = np.bincount(progs.ops, minlength=256).astype(np.float64) - folded_op_counts(progs)
+    interpreter runs: folded constant subexpressions left out when folded), every operator at
+    its measured throughput (beagle_measure_op_rates), leaves free."""
+    counts = np.bincount(progs.ops, minlength=256).astype(np.float64)
+    if folded:
+        counts -= folded_op_counts(progs)
     return sum(counts[op] * N / r for op, r in rates.items())
 
 
@@ -597,7 +619,9 @@ def sub_c1(beagle, synth, torch, stream, flush, args, sm_mhz, sms, rates):
            "p50_ms": _pctl(r["ms"], 0.5), "p99_ms": _pctl(r["ms"], 0.99),
            "fp64": {"value": ev / (statistics.median(r["ms64"]) / 1e3) / 1e9},
            "roofline": roofline_line(ev, r["kernel_s"], [(pr.programs, pr.N)], sm_mhz, sms,
-                                     ev / straight_line_peak(pr.programs, pr.N, rates) / 1e9),
+                                     ev / straight_line_peak(pr.programs, pr.N, rates,
+                                                             launch_folds(pr.programs.P, pr.N)) / 1e9,
+                                     launch_folds(pr.programs.P, pr.N)),
            "parity_full_population": parity_gates(r["g32"], r["g64"], o)}
     r["ds"].release()
     return out
@@ -619,7 +643,9 @@ def sub_c2(beagle, synth, torch, stream, flush, args, sm_mhz, sms, rates):
            "e2e": {"value": ev / e2e["seconds"] / 1e9, "unit": "GPoPs",
                    "h2d_bytes_per_step": e2e["h2d"], "d2h_bytes_per_step": e2e["d2h"]},
            "roofline": roofline_line(ev, r["kernel_s"], [(pr.programs, pr.N)], sm_mhz, sms,
-                                     ev / straight_line_peak(pr.programs, pr.N, rates) / 1e9),
+                                     ev / straight_line_peak(pr.programs, pr.N, rates,
+                                                             launch_folds(pr.programs.P, pr.N)) / 1e9,
+                                     launch_folds(pr.programs.P, pr.N)),
            "parity_sample": parity_gates(sel(r["g32"]), sel(r["g64"]), o)}
     r["ds"].release()
     return out
@@ -742,7 +768,7 @@ def run_headline(args, rank, world, local):
                                 "cross-tile merge)",
                    "l2": "flushed before every timed step (256 MiB write, outside events)",
                    "parallelism": f"replicas x{world} (independent populations)",
-                   "autotuned": r["tuned"]},
+                   "autotuned": r["tuned"], **folding_info(pr.programs, pr.N)},
         "p50_ms": _pctl(ms, 0.5), "p99_ms": _pctl(ms, 0.99),
         "fp64": {"value": ev / (statistics.median(r["ms64"]) / 1e3) / 1e9, "unit": "GPoPs",
                  "ms_per_step": statistics.median(r["ms64"])},
@@ -750,11 +776,13 @@ def run_headline(args, rank, world, local):
         "fp32c_vs_fp64_path": fp32_vs_fp64_path(r["g32"], r["g64"]),
         "parity": parity,
         "roofline": roofline_line(ev, r["kernel_s"], [(pr.programs, pr.N)], sm_mhz, sms,
-                                  ev / straight_line_peak(pr.programs, pr.N, rates) / 1e9),
+                                  ev / straight_line_peak(pr.programs, pr.N, rates,
+                                                          launch_folds(pr.programs.P, pr.N)) / 1e9,
+                                  launch_folds(pr.programs.P, pr.N)),
         "cpu_baseline": cpu,
         "e2e": {"value": ev / e2e["seconds"] / 1e9, "unit": "GPoPs",
                 "h2d_bytes_per_step": e2e["h2d"], "d2h_bytes_per_step": e2e["d2h"]},
-        "gpu_launches": LAUNCHES_PER_CALL * args.steps,
+        "gpu_launches": launches_per_call(pr.programs.P, pr.N) * args.steps,
         "clocks": clk,
         "workloads": subs,
     }
@@ -802,8 +830,8 @@ def run_single(args, rank, world, local):
         line = {"value": sub.pop("value"), "steps": sub.pop("steps"),
                 "warmup": sub.pop("warmup"), "ms_per_step": sub.pop("ms_per_step"),
                 "config": {"workload": sub.pop("workload"), "l2": "256 MiB flush per step"},
-                **sub, "gpu_launches": LAUNCHES_PER_CALL * sub["scoring_launches_per_step"] *
-                args.steps, "clocks": clk}
+                **sub, "gpu_launches": 6 * sub["scoring_launches_per_step"] * args.steps,
+                "clocks": clk}
     else:
         maker = {"c1": synth.make_c1, "c2": synth.make_c2, "c3": synth.make_c3}[args.workload]
         pr = maker(P=args.P) if args.P else maker()
@@ -818,16 +846,20 @@ def run_single(args, rank, world, local):
                 "p50_ms": _pctl(r["ms"], 0.5), "p99_ms": _pctl(r["ms"], 0.99),
                 "config": {"workload": desc, "P": pr.programs.P, "N": pr.N, "d": pr.d,
                            "node_evals_per_step": ev, "autotuned": r["tuned"],
-                           "l2": "256 MiB flush before every step"},
+                           "l2": "256 MiB flush before every step",
+                           **folding_info(pr.programs, pr.N)},
                 "fp64": ({"value": ev / (statistics.median(r["ms64"]) / 1e3) / 1e9}
                          if r["ms64"] else None),
                 "fp32c_vs_fp64_path": fp32_vs_fp64_path(r["g32"], r["g64"]) if r["g64"] else None,
                 "roofline": roofline_line(ev, r["kernel_s"], [(pr.programs, pr.N)], sm_mhz, sms,
-                                          ev / straight_line_peak(pr.programs, pr.N, rates) / 1e9),
+                                          ev / straight_line_peak(pr.programs, pr.N, rates,
+                                                                  launch_folds(pr.programs.P, pr.N)) / 1e9,
+                                          launch_folds(pr.programs.P, pr.N)),
                 "e2e": {"value": ev / e2e["seconds"] / 1e9, "unit": "GPoPs",
                         "h2d_bytes_per_step": e2e["h2d"], "d2h_bytes_per_step": e2e["d2h"]},
                 "cpu_baseline": cpu_baseline(pr, args.cpu_seconds),
-                "gpu_launches": LAUNCHES_PER_CALL * args.steps, "clocks": r["clk"]}
+                "gpu_launches": launches_per_call(pr.programs.P, pr.N) * args.steps,
+                "clocks": r["clk"]}
         r["ds"].release()
     if rank == 0:
         print(json.dumps({**base, **line}), flush=True)

@@ -41,7 +41,7 @@ def test_folded_op_counts_match_a_sequential_fold():
     too; programs with COPY/PASTE are left alone)."""
     rng = np.random.default_rng(5)
     progs = S.gen_programs(rng, 400, 3, 60, 3, unary=S.ALL_UNARY, binary=S.ALL_BINARY)
-    progs = S.with_registers(progs, 3, 0.2, 2)
+    progs = S.with_registers(progs, 3, 0.2, 2)   # register programs are not folded
     got = bench.folded_op_counts(progs)
     want = np.zeros(256, np.int64)
     un = set(range(S.SIN, S.SQUARE + 1)) | set(range(S.POW + 1, S.TANH + 1))
