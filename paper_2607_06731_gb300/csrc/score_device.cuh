@@ -488,11 +488,11 @@ __device__ __forceinline__ int process_program_kind(const JobDev &J, int64_t q, 
     if constexpr (sizeof(T) == 4) {
         // One pass, around the mean m0 of the tile's first 128 outputs: the finalize merge
         // cancels about as little around m0 as around the tile mean. sum e^2 has positive terms
-        // only and is a plain fp32 sum (relative error below 22 u: 16 terms a lane, then 5
+        // only and is a plain fp32 sum (relative error below 15 u: 8 terms a pair half, then 6
         // pairwise steps); the centred sums are compensated. An overflow anywhere in these
         // unscaled sums leaves an infinity or a NaN in them; then the two-pass form below,
         // which scales the terms, runs instead (outputs or targets near 2^60 and above). The
-        // outputs are all equal exactly when the sum of |f - f_0| is 0 (no flush to zero).
+        // outputs are all equal exactly when every f - f_0 is +0 or -0 (no flush to zero).
         float h0[4];
         vals.get4(0, lane, h0);
         const int n0 = min(nval, 128);
@@ -504,36 +504,62 @@ __device__ __forceinline__ int process_program_kind(const JobDev &J, int64_t q, 
         for (int o = 16; o >= 1; o >>= 1) s0 += __shfl_xor_sync(kFull, s0, o);
         const float m0 = s0 / static_cast<float>(n0);
         const float fa = __shfl_sync(kFull, h0[0], 0);
-        float se1 = 0.0f, ad = 0.0f;
-        KahanF sd1, sdd1, sdy1;
+        // Lane pairs of cases (4l, 4l+1) and (4l+2, 4l+3) run through f32x2 instructions: each
+        // half of every accumulator is its own sum, merged before the warp reduction. A case is
+        // unlike case 0 when f - f_0 has a nonzero magnitude (an OR of its bits, sign masked).
+        const float2 m02 = make_float2(m0, m0), fa2 = make_float2(fa, fa);
+        float2 se2 = make_float2(0.0f, 0.0f);
+        uint32_t dbits = 0u;
+        KahanF2 sd2, sdd2, sdy2;
+        auto pair_stats = [&](float2 f, float2 y, float2 yc, uint32_t kx, uint32_t ky) {
+            const float2 e = sub2(f, y);
+            se2 = __ffma2_rn(e, e, se2);
+            const float2 d = sub2(f, fa2);
+            dbits |= (__float_as_uint(d.x) & kx) | (__float_as_uint(d.y) & ky);
+            const float2 dv = sub2(f, m02), dvn = sub2(m02, f);   // dvn = -dv exactly
+            sd2.add(dv);
+            sdd2.add_prod(dv, dvn, dv);
+            sdy2.add_prod(dv, dvn, yc);
+        };
         vals.for_halves(halves, lane, [&](int h, const T (&v)[4]) {
             const float4 y4 = row4(yrow, h);
             const float4 yc4 = row4(ycrow, h);
+            if (h * 128 + 128 <= nval) {   // a full half (warp-uniform)
+                pair_stats(make_float2(v[0], v[1]), make_float2(y4.x, y4.y),
+                           make_float2(yc4.x, yc4.y), ~0u, ~0u);
+                pair_stats(make_float2(v[2], v[3]), make_float2(y4.z, y4.w),
+                           make_float2(yc4.z, yc4.w), ~0u, ~0u);
+            } else {
+                // The ragged half: a case past the end enters as f = y = m0, yc = 0 (every term
+                // exactly 0) with its f - f_0 bits dropped.
+                float f[4], y[4], yc[4];
+                uint32_t keep[4];
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                if (h * 128 + lane * 4 + j < nval) {
-                    const float fi = v[j];
-                    const float e = fi - elem(y4, j);
-                    se1 = fmaf(e, e, se1);
-                    ad += fabsf(fi - fa);
-                    const float dv = fi - m0;
-                    sd1.add(dv);
-                    sdd1.add_prod(dv, dv);
-                    sdy1.add_prod(dv, elem(yc4, j));
+                for (int j = 0; j < 4; ++j) {
+                    const bool in = h * 128 + lane * 4 + j < nval;
+                    f[j] = in ? v[j] : m0;
+                    y[j] = in ? elem(y4, j) : m0;
+                    yc[j] = in ? elem(yc4, j) : 0.0f;
+                    keep[j] = in ? ~0u : 0u;
                 }
+                pair_stats(make_float2(f[0], f[1]), make_float2(y[0], y[1]),
+                           make_float2(yc[0], yc[1]), keep[0], keep[1]);
+                pair_stats(make_float2(f[2], f[3]), make_float2(y[2], y[3]),
+                           make_float2(yc[2], yc[3]), keep[2], keep[3]);
             }
         });
-        const bool nc = __any_sync(kFull, ad != 0.0f);
+        const bool nc = __any_sync(kFull, (dbits & 0x7fffffffu) != 0u);
+        float se1 = se2.x + se2.y;
 #pragma unroll
         for (int o = 16; o >= 1; o >>= 1) se1 += __shfl_xor_sync(kFull, se1, o);
+        KahanF sd1, sdd1, sdy1;
         if (nc) {
+            sd1 = sd2.merged();
+            sdd1 = sdd2.merged();
+            sdy1 = sdy2.merged();
             sd1.warp_allreduce();
             sdd1.warp_allreduce();
             sdy1.warp_allreduce();
-        } else {
-            sd1 = KahanF();
-            sdd1 = KahanF();
-            sdy1 = KahanF();
         }
         // Identical on every lane (the reductions are symmetric), so the branch is uniform.
         const float chk = se1 + (sd1.s + sd1.c) + (sdd1.s + sdd1.c) + (sdy1.s + sdy1.c);
