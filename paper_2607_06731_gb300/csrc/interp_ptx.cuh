@@ -152,43 +152,19 @@ namespace beagle {
     "MULX_%=, PDIVX_%=, ADDC_%=, MULC_%=, PDIVC_%=, END_%=, POW_%=, SIGN_%=, CUBE_%=, "     \
     "CBRT_%=, TAN_%=, ASIN_%=, ACOS_%=, ATAN_%=, TANH_%=, PASTE_%=, END_%=;\n\t"           \
     BG4_DISPATCH                                                                           \
+    /* The handlers the paper's operator set uses come first, in one block, and the rest   \
+       (stack shuffles, the rest of Table 3, the exits) after it: the interpreter's speed   \
+       depends on the instruction footprint of the code it runs. */                        \
     "PUSHX_%=:\n\t" BG4_ROW BG4_XA BG4_STROW "ld.shared.v2.b64 {%0, %1}, [xa];\n\t"         \
     BG4_DISPATCH                                                                           \
     "PUSHC_%=:\n\t" BG4_ROW BG4_STROW "mov.b64 %0, {%7, %7};\n\tmov.b64 %1, %0;\n\t"        \
     BG4_DISPATCH                                                                           \
-    "DUP_%=:\n\t" BG4_ROW BG4_STROW BG4_DISPATCH                                           \
-    "SWAP_%=:\n\t" BG4_ROW BG4_LDROW_A BG4_STROW "mov.b64 %0, A01;\n\tmov.b64 %1, A23;\n\t"  \
-    BG4_DISPATCH                                                                           \
-    "DEL_%=:\n\t" BG4_ROW BG4_LDROW_T BG4_DISPATCH                                         \
     /* top = s top + a: a +- top with s = +-1, rounded once like an add or a subtraction */ \
     "ADDSUB_%=:\n\t" BG4_ROW "mov.b64 C2, {%7, %7};\n\t" BG4_LDROW_A                        \
     "fma.rn.f32x2 %0, C2, %0, A01;\n\tfma.rn.f32x2 %1, C2, %1, A23;\n\t"                   \
     BG4_TRACK BG4_DISPATCH                                                                 \
     "MUL_%=:\n\t" BG4_ROW BG4_LDROW_A                                                      \
     "mul.rn.f32x2 %0, A01, %0;\n\tmul.rn.f32x2 %1, A23, %1;\n\t" BG4_TRACK BG4_DISPATCH    \
-    "PDIV_%=:\n\t" BG4_ROW BG4_LDROW_A                                                     \
-    BG4_PDIV2("%0", "A01", "%0") BG4_PDIV2("%1", "A23", "%1") BG4_TRACK BG4_DISPATCH       \
-    /* sin and cos: arguments above 65536 in magnitude or NaN on any lane leave the loop   \
-       (the caller takes CUDA's sinf / cosf on those lanes); no tracking: the results of a    \
-       valid operand are bounded */                                                        \
-    "SIN_%=:\n\tmov.u32 qoff, 0xB4C00000;\n\tmov.u32 sccode, 8;\n\tbra.uni SC_%=;\n"          \
-    "COS_%=:\n\tmov.u32 qoff, 0xB4C00001;\n\tmov.u32 sccode, 9;\n"                            \
-    "SC_%=:\n\t" BG4_UNPACK                                                                 \
-    "abs.f32 z, t0;\n\tabs.f32 d0, t1;\n\tmax.NaN.f32 z, z, d0;\n\t"                          \
-    "abs.f32 d0, t2;\n\tmax.NaN.f32 z, z, d0;\n\tabs.f32 d0, t3;\n\tmax.NaN.f32 z, z, d0;\n\t"  \
-    "setp.gtu.f32 q0, z, " BG_PTX_F32(BG_K_SINCOS_LIMIT) ";\n\t"                              \
-    "vote.sync.any.pred q1, q0, 0xffffffff;\n\t@q1 bra.uni SCX_%=;\n\t"                      \
-    BG4_SINCOS2("%0") BG4_SINCOS2("%1") BG4_DISPATCH                                       \
-    "SCX_%=:\n\tmov.u32 %9, sccode;\n\tbra.uni OUT_%=;\n"                                     \
-    BG4_EXIT("EXP", 10)                                                                    \
-    /* the protected log: no tracking (|ln|v|| <= 69.1 for a valid operand) */              \
-    "PLOG_%=:\n\t" BG4_PLOG2("%0") BG4_PLOG2("%1") BG4_DISPATCH                            \
-    "PSQRT_%=:\n\t" BG4_UNPACK                                                             \
-    "abs.f32 t0, t0;\n\tsqrt.rn.f32 t0, t0;\n\tabs.f32 t1, t1;\n\tsqrt.rn.f32 t1, t1;\n\t" \
-    "abs.f32 t2, t2;\n\tsqrt.rn.f32 t2, t2;\n\tabs.f32 t3, t3;\n\tsqrt.rn.f32 t3, t3;\n\t" \
-    BG4_PACK BG4_DISPATCH                                                                  \
-    "SQUARE_%=:\n\t" "mul.rn.f32x2 %0, %0, %0;\n\tmul.rn.f32x2 %1, %1, %1;\n\t"             \
-    BG4_TRACK BG4_DISPATCH                                                                 \
     /* fused leaf + binary operator: top = s x + top; top + c (c negated for a subtraction); \
        each with its own copy of the arithmetic (sharing one copy through a branch measured \
        0.5 % slower) */                                                                    \
@@ -201,24 +177,54 @@ namespace beagle {
     "mul.rn.f32x2 %0, %0, A01;\n\tmul.rn.f32x2 %1, %1, A23;\n\t" BG4_TRACK BG4_DISPATCH    \
     "MULC_%=:\n\t" "mov.b64 C2, {%7, %7};\n\t"                                             \
     "mul.rn.f32x2 %0, %0, C2;\n\tmul.rn.f32x2 %1, %1, C2;\n\t" BG4_TRACK BG4_DISPATCH      \
-    /* fused division by an input or a constant: one shared copy of the divisions (the     \
-       interpreter's speed depends on its instruction footprint) */                        \
+    /* the divisions share one copy of the arithmetic, top = top / A: the stack division   \
+       moves its operands there (the stack row to the top, the top to A), the fused ones    \
+       load A from the input row or the constant word */                                   \
+    "PDIV_%=:\n\t" BG4_ROW "mov.b64 A01, %0;\n\tmov.b64 A23, %1;\n\t" BG4_LDROW("a")       \
+    "mov.b64 %0, {a0, a1};\n\tmov.b64 %1, {a2, a3};\n\tbra.uni DIVTA_%=;\n"                 \
     "PDIVX_%=:\n\t" BG4_XA BG4_LDX_A "bra.uni DIVTA_%=;\n"                                  \
     "PDIVC_%=:\n\t" "mov.b64 A01, {%7, %7};\n\tmov.b64 A23, A01;\n"                          \
     "DIVTA_%=:\n\t"                                                                         \
     BG4_PDIV2("%0", "%0", "A01") BG4_PDIV2("%1", "%1", "A23") BG4_TRACK BG4_DISPATCH       \
-    /* the rest of Table 3: SIGN (|v| unchanged, nothing to track), CUBE ((a a) a), PASTE  \
-       (push the top, load the register's row, its index in the constant word) */          \
-    BG4_EXIT("POW", 21)                                                                    \
+    "SQUARE_%=:\n\t" "mul.rn.f32x2 %0, %0, %0;\n\tmul.rn.f32x2 %1, %1, %1;\n\t"             \
+    BG4_TRACK BG4_DISPATCH                                                                 \
+    /* sin and cos: arguments above 65536 in magnitude or NaN on any lane leave the loop   \
+       (the caller takes CUDA's sinf / cosf on those lanes); no tracking: the results of a    \
+       valid operand are bounded */                                                        \
+    "SIN_%=:\n\tmov.u32 qoff, 0xB4C00000;\n\tmov.u32 sccode, 8;\n\tbra.uni SC_%=;\n"          \
+    "COS_%=:\n\tmov.u32 qoff, 0xB4C00001;\n\tmov.u32 sccode, 9;\n"                            \
+    "SC_%=:\n\t" BG4_UNPACK                                                                 \
+    "abs.f32 z, t0;\n\tabs.f32 d0, t1;\n\tmax.NaN.f32 z, z, d0;\n\t"                          \
+    "abs.f32 d0, t2;\n\tmax.NaN.f32 z, z, d0;\n\tabs.f32 d0, t3;\n\tmax.NaN.f32 z, z, d0;\n\t"  \
+    "setp.gtu.f32 q0, z, " BG_PTX_F32(BG_K_SINCOS_LIMIT) ";\n\t"                              \
+    "vote.sync.any.pred q1, q0, 0xffffffff;\n\t@q1 bra.uni SCX_%=;\n\t"                      \
+    BG4_SINCOS2("%0") BG4_SINCOS2("%1") BG4_DISPATCH                                       \
+    /* the protected log: no tracking (|ln|v|| <= 69.1 for a valid operand) */              \
+    "PLOG_%=:\n\t" BG4_PLOG2("%0") BG4_PLOG2("%1") BG4_DISPATCH                            \
+    "PSQRT_%=:\n\t" BG4_UNPACK                                                             \
+    "abs.f32 t0, t0;\n\tsqrt.rn.f32 t0, t0;\n\tabs.f32 t1, t1;\n\tsqrt.rn.f32 t1, t1;\n\t" \
+    "abs.f32 t2, t2;\n\tsqrt.rn.f32 t2, t2;\n\tabs.f32 t3, t3;\n\tsqrt.rn.f32 t3, t3;\n\t" \
+    BG4_PACK BG4_DISPATCH                                                                  \
+    /* exp leaves the loop for CUDA's expf (an in-loop polynomial form measured slower:    \
+       the loop's larger code costs more in instruction fetch than the exit) */             \
+    BG4_EXIT("EXP", 10)                                                                    \
+    "END_%=:\n\tmov.u32 %9, 0;\n\tbra.uni OUT_%=;\n"                                          \
+    /* the rest: DUP, SWAP, DEL; SIGN (|v| unchanged, nothing to track), CUBE ((a a) a),     \
+       PASTE (push the top, load the register's row, its index in the constant word); the   \
+       operators that leave the loop */                                                    \
+    "DUP_%=:\n\t" BG4_ROW BG4_STROW BG4_DISPATCH                                           \
+    "SWAP_%=:\n\t" BG4_ROW BG4_LDROW_A BG4_STROW "mov.b64 %0, A01;\n\tmov.b64 %1, A23;\n\t"  \
+    BG4_DISPATCH                                                                           \
+    "DEL_%=:\n\t" BG4_ROW BG4_LDROW_T BG4_DISPATCH                                         \
     "SIGN_%=:\n\tmov.b64 KA, " BG_PTX_PAIR(BG_K_NONE) ";\n\t"                                 \
     "mul.rn.f32x2 %0, %0, KA;\n\tmul.rn.f32x2 %1, %1, KA;\n\t" BG4_DISPATCH                \
     "CUBE_%=:\n\t" "mul.rn.f32x2 A01, %0, %0;\n\tmul.rn.f32x2 A23, %1, %1;\n\t"             \
     "mul.rn.f32x2 %0, A01, %0;\n\tmul.rn.f32x2 %1, A23, %1;\n\t" BG4_TRACK BG4_DISPATCH    \
-    BG4_EXIT("CBRT", 24) BG4_EXIT("TAN", 25) BG4_EXIT("ASIN", 26) BG4_EXIT("ACOS", 27)     \
-    BG4_EXIT("ATAN", 28) BG4_EXIT("TANH", 29)                                              \
     "PASTE_%=:\n\t" BG4_ROW BG4_STROW "mad.lo.u32 rp, %7, 4, %11;\n\t" BG4_LDROW_T           \
     BG4_DISPATCH                                                                           \
-    "END_%=:\n\tmov.u32 %9, 0;\n"                                                          \
+    "SCX_%=:\n\tmov.u32 %9, sccode;\n\tbra.uni OUT_%=;\n"                                     \
+    BG4_EXIT("POW", 21) BG4_EXIT("CBRT", 24) BG4_EXIT("TAN", 25) BG4_EXIT("ASIN", 26)      \
+    BG4_EXIT("ACOS", 27) BG4_EXIT("ATAN", 28) BG4_EXIT("TANH", 29)                         \
     "OUT_%=:\n\t"                                                                          \
     "}"
 
@@ -272,21 +278,29 @@ __device__ __forceinline__ unsigned long long f2_pair(float2 v) {
 
 // The operators that leave the loop, on 4 values of a lane (two pairs) and their 4 trackers:
 // code is the handler id; base is the tensor-memory address of POW's base operands (the 4
-// values of its stack row, read only for POW).
-__device__ __forceinline__ void apply_exit4(uint32_t code, uint32_t base,
-                                            unsigned long long &pa, unsigned long long &pb,
-                                            float &m0, float &m1, float &m2, float &m3) {
+// values of its stack row, read only for POW). exp, the one exit of the paper's operator set
+// that every program may take, runs in line; the others (sin and cos of large arguments, the
+// rest of Table 3, the 8-case loop's log) run out of line, so that their code does not take
+// room in the instruction cache next to the loop.
+struct Lane4 {
+    unsigned long long pa, pb;
+    float m0, m1, m2, m3;
+};
+
+static __device__ __noinline__ Lane4 exit_values4(uint32_t code, uint32_t base, Lane4 s) {
     using A = Arith<float>;
-    float2 a = pair_f2(pa), b = pair_f2(pb);
-    if (code >= H_POW) {   // the rest of Table 3, out of line
+    float2 a = pair_f2(s.pa), b = pair_f2(s.pb);
+    if (code >= H_POW) {   // the rest of Table 3
         float4 bv = make_float4(0.f, 0.f, 0.f, 0.f);
         if (code == H_POW) tmem_ld_row4(base, bv.x, bv.y, bv.z, bv.w);
         const float4 r = ext_values4(code, make_float4(a.x, a.y, b.x, b.y), bv);
         a = make_float2(r.x, r.y);
         b = make_float2(r.z, r.w);
-    } else if (code == H_EXP) {
-        a = make_float2(A::exp_(a.x), A::exp_(a.y));
-        b = make_float2(A::exp_(b.x), A::exp_(b.y));
+        // cbrt, atan and tanh of a valid value are valid too; tracking them changes nothing
+        s.m0 = A::track(s.m0, a.x);
+        s.m1 = A::track(s.m1, a.y);
+        s.m2 = A::track(s.m2, b.x);
+        s.m3 = A::track(s.m3, b.y);
     } else if (code == H_PLOG) {
         a = plog2(a);
         b = plog2(b);
@@ -294,17 +308,35 @@ __device__ __forceinline__ void apply_exit4(uint32_t code, uint32_t base,
         sincos4_paired(a, b, static_cast<int>(code) - H_SIN);
     }
     // sin, cos and the protected log of a valid value are finite and bounded (|ln|v|| <= 69.1
-    // for |v| <= 1e30), and an invalid operand was recorded when it was pushed, so only exp
-    // and the rest of Table 3 can produce a new invalid value here (cbrt, atan and tanh of a
-    // valid value are valid too; tracking them changes nothing).
-    if (code == H_EXP || code >= H_POW) {
+    // for |v| <= 1e30), and an invalid operand was recorded when it was pushed: no tracking.
+    s.pa = f2_pair(a);
+    s.pb = f2_pair(b);
+    return s;
+}
+
+__device__ __forceinline__ void apply_exit4(uint32_t code, uint32_t base,
+                                            unsigned long long &pa, unsigned long long &pb,
+                                            float &m0, float &m1, float &m2, float &m3) {
+    using A = Arith<float>;
+    if (code == H_EXP) {
+        float2 a = pair_f2(pa), b = pair_f2(pb);
+        a = make_float2(A::exp_(a.x), A::exp_(a.y));
+        b = make_float2(A::exp_(b.x), A::exp_(b.y));
         m0 = A::track(m0, a.x);
         m1 = A::track(m1, a.y);
         m2 = A::track(m2, b.x);
         m3 = A::track(m3, b.y);
+        pa = f2_pair(a);
+        pb = f2_pair(b);
+        return;
     }
-    pa = f2_pair(a);
-    pb = f2_pair(b);
+    const Lane4 s = exit_values4(code, base, Lane4{pa, pb, m0, m1, m2, m3});
+    pa = s.pa;
+    pb = s.pb;
+    m0 = s.m0;
+    m1 = s.m1;
+    m2 = s.m2;
+    m3 = s.m3;
 }
 
 // prog: shared address of the packed program (bits 24-28 of each token: the next token's
