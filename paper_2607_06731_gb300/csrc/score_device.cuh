@@ -488,8 +488,8 @@ __device__ __forceinline__ int process_program_kind(const JobDev &J, int64_t q, 
     if constexpr (sizeof(T) == 4) {
         // One pass, around the mean m0 of the tile's first 128 outputs: the finalize merge
         // cancels about as little around m0 as around the tile mean. sum e^2 has positive terms
-        // only and is a plain fp32 sum (relative error below 15 u: 8 terms a pair half, then 6
-        // pairwise steps); the centred sums are compensated. An overflow anywhere in these
+        // only and is a plain fp32 sum over each lane's pair half (8 terms, relative error below
+        // 8 u), compensated beyond; the centred sums are compensated throughout. An overflow anywhere in these
         // unscaled sums leaves an infinity or a NaN in them; then the two-pass form below,
         // which scales the terms, runs instead (outputs or targets near 2^60 and above). The
         // outputs are all equal exactly when every f - f_0 is +0 or -0 (no flush to zero).
@@ -549,33 +549,37 @@ __device__ __forceinline__ int process_program_kind(const JobDev &J, int64_t q, 
             }
         });
         const bool nc = __any_sync(kFull, (dbits & 0x7fffffffu) != 0u);
-        float se1 = se2.x + se2.y;
-#pragma unroll
-        for (int o = 16; o >= 1; o >>= 1) se1 += __shfl_xor_sync(kFull, se1, o);
-        KahanF sd1, sdd1, sdy1;
+        // The four sums (se, sd, sdd, sdy) over the warp by halving: after the step over lane
+        // bit 4 each half of the warp holds two of them, after the step over bit 3 each group
+        // of 8 lanes one (lanes 8g..8g+7 sum g), merged over its group in three more steps.
+        KahanF q0, q1, q2, q3;
+        q0.s = se2.x;
+        q0.merge(se2.y, 0.0f);
         if (nc) {
-            sd1 = sd2.merged();
-            sdd1 = sdd2.merged();
-            sdy1 = sdy2.merged();
-            sd1.warp_allreduce();
-            sdd1.warp_allreduce();
-            sdy1.warp_allreduce();
+            q1 = sd2.merged();
+            q2 = sdd2.merged();
+            q3 = sdy2.merged();
         }
-        // Identical on every lane (the reductions are symmetric), so the branch is uniform.
-        const float chk = se1 + (sd1.s + sd1.c) + (sdd1.s + sdd1.c) + (sdy1.s + sdy1.c);
-        if (isfinite(chk)) {
-            if (lane == 0) {
-                uint32_t w[kNumFields];
-                w[kMean] = __float_as_uint(nc ? m0 : fa);
-                w[kMean64] = 0u;
-                w[kSe2] = __float_as_uint(se1);
-                w[kSe2 + 1] = 0u;
-                put_pair(w + kSd, sd1);
-                put_pair(w + kSdd, sdd1);
-                put_pair(w + kSdy, sdy1);
-                w[kTileFlags] = nc ? TF_NONCONST : 0u;
+        const bool hi16 = (lane & 16) != 0, hi8 = (lane & 8) != 0;
+        KahanF ka = hi16 ? q2 : q0, kb = hi16 ? q3 : q1;
+        ka.merge(kf_shfl_xor(hi16 ? q0 : q2, 16));
+        kb.merge(kf_shfl_xor(hi16 ? q1 : q3, 16));
+        KahanF k = hi8 ? kb : ka;
+        k.merge(kf_shfl_xor(hi8 ? ka : kb, 8));
 #pragma unroll
-                for (int f = 0; f < kNumFields; ++f) *field(f) = w[f];
+        for (int o = 4; o >= 1; o >>= 1) k.merge(kf_shfl_xor(k, o));
+        static_assert(kSd == kSe2 + 2 && kSdd == kSe2 + 4 && kSdy == kSe2 + 6,
+                      "the sums' fields follow one another");
+        if (__all_sync(kFull, isfinite(k.s + k.c))) {
+            if ((lane & 7) == 0) {
+                const int g = lane >> 3;
+                *field(kSe2 + 2 * g) = __float_as_uint(k.s);
+                *field(kSe2 + 2 * g + 1) = __float_as_uint(k.c);
+            }
+            if (lane == 0) {
+                *field(kMean) = __float_as_uint(nc ? m0 : fa);
+                *field(kMean64) = 0u;
+                *field(kTileFlags) = nc ? TF_NONCONST : 0u;
             }
             __syncwarp();
             return 0;
