@@ -159,14 +159,15 @@ ALGO_UNITS = {1: (1, 0, 1), 2: (1, 0, 1), 3: (1, 0, 1), 10: (1, 0, 1),
 LANES_PER_SM_CLK = {"fp32": 128, "mufu": 32, "alu": 64, "issue": 128}
 
 
-def folded_op_counts(progs):
+def folded_op_counts(progs, w=None):
     """Per opcode, the operators the packing kernel folds (constant subexpressions, evaluated
     once per call instead of on every case): the constness of every stack value followed
     through all programs at once, token position by token position. As on the device, only
-    programs of leaves, unary and binary operators are folded."""
+    programs of leaves, unary and binary operators are folded. w: optional per-program
+    weights (each program's folded operators count w[p] times)."""
     from paper_2607_06731_gb300 import synth as S
     P = progs.P
-    out = np.zeros(256, np.int64)
+    out = np.zeros(256, np.float64 if w is not None else np.int64)
     if P == 0:
         return out
     L = progs.lengths.astype(np.int64)
@@ -199,8 +200,16 @@ def folded_op_counts(progs):
         per.append((act[f], op[f]))
     for idx, op in per:
         keep = ~other[idx]
-        np.add.at(out, op[keep], 1)
+        np.add.at(out, op[keep], 1 if w is None else w[idx[keep]])
     return out
+
+
+def op_counts(progs, w=None):
+    """Per opcode, the operators of the programs (each program's counted w[p] times)."""
+    if w is None:
+        return np.bincount(progs.ops, minlength=256).astype(np.float64)
+    tw = np.repeat(np.asarray(w, np.float64), progs.lengths.astype(np.int64))
+    return np.bincount(progs.ops, weights=tw, minlength=256)
 
 
 def removed_tokens(folded):
@@ -217,29 +226,52 @@ def launch_folds(P: int, N: int) -> bool:
     return P * N >= PACKED_LAUNCH_CASES
 
 
-def folding_info(progs, N):
-    """The config entry on constant folding: node evaluations of the original programs (the
-    metric's count) and of the programs the interpreter runs."""
-    ev = float(progs.lengths.sum(dtype=np.int64)) * N
-    if not launch_folds(progs.P, N):
-        return {"constant_folding": "off (launch below 2^24 program-cases)",
-                "executed_node_evals_per_step": ev}
-    rm = removed_tokens(folded_op_counts(progs))
-    return {"constant_folding": ("on: constant subexpressions evaluated once per call by the "
-                                 "packing kernel, same bits; value counts the original "
-                                 "programs' node evaluations"),
-            "executed_node_evals_per_step": ev - float(rm) * N,
-            "folded_token_fraction": rm / max(1.0, float(progs.lengths.sum(dtype=np.int64)))}
+def case_weights(cases_run, N):
+    """Per program, the fraction of the N fitness cases the scoring call evaluated
+    (beagle_count_cases), or None (every case)."""
+    return None if cases_run is None else np.asarray(cases_run, np.float64) / float(N)
+
+
+def work_info(progs, N, cases_run=None, ms=None):
+    """The config entries on the work a step does: node evaluations of the original programs
+    (the metric's count), and of what the interpreter ran: constant subexpressions folded
+    once per call, and the cases each program ran (an invalid program stops at the first
+    case tile pass that meets an invalid value; its later tiles are not run)."""
+    tok = float(progs.lengths.sum(dtype=np.int64))
+    ev = tok * N
+    w = case_weights(cases_run, N)
+    folds = launch_folds(progs.P, N)
+    ran = float(np.dot(progs.lengths.astype(np.float64), w)) if w is not None else tok
+    rm = removed_tokens(folded_op_counts(progs, w)) if folds else 0.0
+    out = {"constant_folding": ("on: constant subexpressions evaluated once per call by the "
+                                "packing kernel, same bits" if folds else
+                                "off (launch below 2^24 program-cases)"),
+           "invalid_early_exit": ("on: a program stops at the first case pass with an invalid "
+                                  "value, later tiles of a program found invalid are skipped; "
+                                  "same bits (the validity rule makes it invalid whatever its "
+                                  "other cases give)" if w is not None else "not measured"),
+           "value_counts": "node evaluations of the original programs on every case",
+           "executed_node_evals_per_step": (ran - float(rm)) * N}
+    if folds:
+        out["folded_token_fraction"] = removed_tokens(folded_op_counts(progs)) / max(1.0, tok)
+    if w is not None:
+        out["executed_case_fraction"] = float(np.sum(cases_run)) / max(1.0, float(progs.P) * N)
+        if ms:
+            out["executed_gpops"] = out["executed_node_evals_per_step"] / (ms / 1e3) / 1e9
+    return out
 
 
 def algorithmic_units(progs_list, folded=True):
-    """Lane operations of each pipe over populations [(programs, N)], of the operators the
-    interpreter runs (the folded constant subexpressions left out when folded)."""
+    """Lane operations of each pipe over populations [(programs, N[, w])], of the operators
+    the interpreter runs: the folded constant subexpressions left out when folded, and each
+    program's operators on the fraction w[p] of the cases it ran (all when w is absent)."""
     tot = {"fp32": 0.0, "mufu": 0.0, "alu": 0.0}
-    for progs, N in progs_list:
-        counts = np.bincount(progs.ops, minlength=256).astype(np.float64)
+    for item in progs_list:
+        progs, N = item[0], item[1]
+        w = item[2] if len(item) > 2 else None
+        counts = op_counts(progs, w)
         if folded:
-            counts -= folded_op_counts(progs)
+            counts -= folded_op_counts(progs, w)
         for op, (f, m, a) in ALGO_UNITS.items():
             tot["fp32"] += counts[op] * N * f
             tot["mufu"] += counts[op] * N * m
@@ -257,7 +289,7 @@ def roofline_time(progs_list, sm_mhz: float, sms: int, folded=True):
     bind = max(t, key=t.get)
     return {"seconds": t[bind], "binding": bind, "per_pipe_ms": {k: v * 1e3 for k, v in t.items()},
             "lane_ops_per_node_eval": units["issue"] / max(1.0, sum(
-                float(p.lengths.sum(dtype=np.int64)) * N for p, N in progs_list))}
+                float(it[0].lengths.sum(dtype=np.int64)) * it[1] for it in progs_list))}
 
 
 def roofline_line(node_evals, kernel_s, progs_list, sm_mhz, sms, peak_straight=None,
@@ -268,9 +300,9 @@ def roofline_line(node_evals, kernel_s, progs_list, sm_mhz, sms, peak_straight=N
     out = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "GPoPs",
            "frac": achieved / peak if achieved else None, "traffic": None,
            "peak_basis": (f"algorithmic lane operations per node evaluation (FP32/MUFU/ALU "
-                          f"units per operator, leaves free) at {LANES_PER_SM_CLK} lanes per "
-                          f"SM per clock, {sms} SMs, {sm_mhz:.0f} MHz measured; binding: "
-                          f"{rt['binding']}"),
+                          f"units per operator, leaves free) of the operators and cases the "
+                          f"kernels ran, at {LANES_PER_SM_CLK} lanes per SM per clock, {sms} "
+                          f"SMs, {sm_mhz:.0f} MHz measured; binding: {rt['binding']}"),
            "per_pipe_ms": rt["per_pipe_ms"],
            "lane_ops_per_node_eval": rt["lane_ops_per_node_eval"],
            "kernel_ms": kernel_s * 1e3 if kernel_s else None}
@@ -280,13 +312,14 @@ def roofline_line(node_evals, kernel_s, progs_list, sm_mhz, sms, peak_straight=N
     return out
 
 
-def straight_line_peak(progs, N, rates, folded=True):
-    """Seconds straight-line compiled code would need for this op mix (the operators the
-    interpreter runs: folded constant subexpressions left out when folded), every operator at
-    its measured throughput (beagle_measure_op_rates), leaves free."""
-    counts = np.bincount(progs.ops, minlength=256).astype(np.float64)
+def straight_line_peak(progs, N, rates, folded=True, w=None):
+    """Seconds straight-line compiled code would need for this op mix (the operators and cases
+    the interpreter runs: folded constant subexpressions left out when folded, each program on
+    the fraction w[p] of the cases it ran), every operator at its measured throughput
+    (beagle_measure_op_rates), leaves free."""
+    counts = op_counts(progs, w)
     if folded:
-        counts -= folded_op_counts(progs)
+        counts -= folded_op_counts(progs, w)
     return sum(counts[op] * N / r for op, r in rates.items())
 
 
@@ -586,6 +619,16 @@ def score_population(beagle, torch, pr, stream, flush, steps, warmup, clocks=Non
     beagle.kernel_timing(False)
     kern_ms, kern_n = beagle.kernel_time()
     g32 = beagle.unpack_fitness(out)
+    # the cases each program ran (the early exit on invalid programs), on one more call
+    # outside the timed region
+    counts = torch.zeros(dp.P, dtype=torch.int64, device="cuda")
+    beagle.count_cases(counts)
+    try:
+        beagle.score_programs(dp, ds, out=torch.empty_like(out), stream=stream)
+        torch.cuda.synchronize()
+    finally:
+        beagle.count_cases(None)
+    cases_run = counts.cpu().numpy()
     g64, ms64 = None, None
     if fp64_steps > 0:
         ms64 = timed_steps(lambda: beagle.score_programs(dp, ds, out=out, precision="fp64",
@@ -595,7 +638,17 @@ def score_population(beagle, torch, pr, stream, flush, steps, warmup, clocks=Non
     # kernel time of the timed steps only (warm-up launches were timed too: drop them)
     kern_avg = kern_ms / max(kern_n, 1) / 1e3
     return {"ds": ds, "dp": dp, "ms": ms, "ms64": ms64, "g32": g32, "g64": g64, "clk": clk,
-            "kernel_s": kern_avg, "tuned": tuned}
+            "kernel_s": kern_avg, "tuned": tuned, "cases_run": cases_run}
+
+
+def roofline_of(ev, r, pr, sm_mhz, sms, rates):
+    """The roofline entry of one timed population (executed operators and cases)."""
+    folds = launch_folds(pr.programs.P, pr.N)
+    w = case_weights(r.get("cases_run"), pr.N)
+    item = (pr.programs, pr.N) if w is None else (pr.programs, pr.N, w)
+    return roofline_line(ev, r["kernel_s"], [item], sm_mhz, sms,
+                         ev / straight_line_peak(pr.programs, pr.N, rates, folds, w) / 1e9,
+                         folds)
 
 
 def fp32_vs_fp64_path(g32, g64):
@@ -618,10 +671,8 @@ def sub_c1(beagle, synth, torch, stream, flush, args, sm_mhz, sms, rates):
            "unit": "GPoPs", "ms_per_step": statistics.mean(r["ms"]),
            "p50_ms": _pctl(r["ms"], 0.5), "p99_ms": _pctl(r["ms"], 0.99),
            "fp64": {"value": ev / (statistics.median(r["ms64"]) / 1e3) / 1e9},
-           "roofline": roofline_line(ev, r["kernel_s"], [(pr.programs, pr.N)], sm_mhz, sms,
-                                     ev / straight_line_peak(pr.programs, pr.N, rates,
-                                                             launch_folds(pr.programs.P, pr.N)) / 1e9,
-                                     launch_folds(pr.programs.P, pr.N)),
+           "roofline": roofline_of(ev, r, pr, sm_mhz, sms, rates),
+           "work": work_info(pr.programs, pr.N, r["cases_run"], statistics.mean(r["ms"])),
            "parity_full_population": parity_gates(r["g32"], r["g64"], o)}
     r["ds"].release()
     return out
@@ -642,10 +693,8 @@ def sub_c2(beagle, synth, torch, stream, flush, args, sm_mhz, sms, rates):
            "fp64": {"value": ev / (statistics.median(r["ms64"]) / 1e3) / 1e9},
            "e2e": {"value": ev / e2e["seconds"] / 1e9, "unit": "GPoPs",
                    "h2d_bytes_per_step": e2e["h2d"], "d2h_bytes_per_step": e2e["d2h"]},
-           "roofline": roofline_line(ev, r["kernel_s"], [(pr.programs, pr.N)], sm_mhz, sms,
-                                     ev / straight_line_peak(pr.programs, pr.N, rates,
-                                                             launch_folds(pr.programs.P, pr.N)) / 1e9,
-                                     launch_folds(pr.programs.P, pr.N)),
+           "roofline": roofline_of(ev, r, pr, sm_mhz, sms, rates),
+           "work": work_info(pr.programs, pr.N, r["cases_run"], statistics.mean(r["ms"])),
            "parity_sample": parity_gates(sel(r["g32"]), sel(r["g64"]), o)}
     r["ds"].release()
     return out
@@ -683,6 +732,18 @@ def sub_c4(beagle, synth, torch, stream, flush, args, sm_mhz, sms, steps=None, c
         for dp, ds, out in items:
             beagle.score_programs(dp, ds, out=out, stream=stream)
     ms1 = timed_steps(one_by_one, 2, 1, stream, flush)
+    # the cases each program ran (early exit on invalid programs), population by population
+    # outside the timed region (the case counter follows single-population calls)
+    weights = []
+    for (dp, ds, out), pr in zip(items, pops):
+        counts = torch.zeros(dp.P, dtype=torch.int64, device="cuda")
+        beagle.count_cases(counts)
+        try:
+            beagle.score_programs(dp, ds, out=out, stream=stream)
+            torch.cuda.synchronize()
+        finally:
+            beagle.count_cases(None)
+        weights.append(case_weights(counts.cpu().numpy(), pr.N))
     plan.destroy()
     for _, ds, _ in items:
         ds.release()
@@ -693,7 +754,11 @@ def sub_c4(beagle, synth, torch, stream, flush, args, sm_mhz, sms, steps=None, c
             "node_evals_per_step": ev, "scoring_launches_per_step": kern_n // 2,
             "one_call_per_population": {"value": ev / (statistics.median(ms1) / 1e3) / 1e9,
                                         "unit": "GPoPs"},
-            "roofline": roofline_line(ev, kern_s, [(pr.programs, pr.N) for pr in pops],
+            "executed_case_fraction": float(
+                sum(float(w.sum()) * pr.N for w, pr in zip(weights, pops)) /
+                max(1.0, sum(float(pr.programs.P) * pr.N for pr in pops))),
+            "roofline": roofline_line(ev, kern_s, [(pr.programs, pr.N, w)
+                                                   for pr, w in zip(pops, weights)],
                                       sm_mhz or 2070.0, sms)}
 
 
@@ -768,17 +833,14 @@ def run_headline(args, rank, world, local):
                                 "cross-tile merge)",
                    "l2": "flushed before every timed step (256 MiB write, outside events)",
                    "parallelism": f"replicas x{world} (independent populations)",
-                   "autotuned": r["tuned"], **folding_info(pr.programs, pr.N)},
+                   "autotuned": r["tuned"], **work_info(pr.programs, pr.N, r["cases_run"], tot_ms / args.steps)},
         "p50_ms": _pctl(ms, 0.5), "p99_ms": _pctl(ms, 0.99),
         "fp64": {"value": ev / (statistics.median(r["ms64"]) / 1e3) / 1e9, "unit": "GPoPs",
                  "ms_per_step": statistics.median(r["ms64"])},
         "fp32c_vs_fp64_speedup": statistics.median(r["ms64"]) / statistics.median(ms),
         "fp32c_vs_fp64_path": fp32_vs_fp64_path(r["g32"], r["g64"]),
         "parity": parity,
-        "roofline": roofline_line(ev, r["kernel_s"], [(pr.programs, pr.N)], sm_mhz, sms,
-                                  ev / straight_line_peak(pr.programs, pr.N, rates,
-                                                          launch_folds(pr.programs.P, pr.N)) / 1e9,
-                                  launch_folds(pr.programs.P, pr.N)),
+        "roofline": roofline_of(ev, r, pr, sm_mhz, sms, rates),
         "cpu_baseline": cpu,
         "e2e": {"value": ev / e2e["seconds"] / 1e9, "unit": "GPoPs",
                 "h2d_bytes_per_step": e2e["h2d"], "d2h_bytes_per_step": e2e["d2h"]},
@@ -847,14 +909,11 @@ def run_single(args, rank, world, local):
                 "config": {"workload": desc, "P": pr.programs.P, "N": pr.N, "d": pr.d,
                            "node_evals_per_step": ev, "autotuned": r["tuned"],
                            "l2": "256 MiB flush before every step",
-                           **folding_info(pr.programs, pr.N)},
+                           **work_info(pr.programs, pr.N, r["cases_run"], statistics.mean(r["ms"]))},
                 "fp64": ({"value": ev / (statistics.median(r["ms64"]) / 1e3) / 1e9}
                          if r["ms64"] else None),
                 "fp32c_vs_fp64_path": fp32_vs_fp64_path(r["g32"], r["g64"]) if r["g64"] else None,
-                "roofline": roofline_line(ev, r["kernel_s"], [(pr.programs, pr.N)], sm_mhz, sms,
-                                          ev / straight_line_peak(pr.programs, pr.N, rates,
-                                                                  launch_folds(pr.programs.P, pr.N)) / 1e9,
-                                          launch_folds(pr.programs.P, pr.N)),
+                "roofline": roofline_of(ev, r, pr, sm_mhz, sms, rates),
                 "e2e": {"value": ev / e2e["seconds"] / 1e9, "unit": "GPoPs",
                         "h2d_bytes_per_step": e2e["h2d"], "d2h_bytes_per_step": e2e["d2h"]},
                 "cpu_baseline": cpu_baseline(pr, args.cpu_seconds),

@@ -415,6 +415,26 @@ beagle_status beagle_get_launch_config(beagle_launch_config *cfg);
  */
 beagle_status beagle_measure_op_rates(double *rates, int32_t n_rates, double seconds_hint,
                                       void *stream);
+
+/*
+ * Early exit on invalid programs (MSE / 1 - r^2 scoring). A program with one invalid value on
+ * one fitness case is invalid (the validity rule above), whatever its other cases give. By
+ * default the scoring kernels use that: a case tile stops at the first 128-case pass (256 at 8
+ * cases per lane) that meets an invalid case, and once some tile has found a program invalid
+ * its later tiles are not run. The results are the same bits either way; the work done, and
+ * so the time, depends on how many programs are invalid and where. enable = 0 turns this off
+ * (every case of every program runs) for the calls that follow, 1 turns it back on.
+ * beagle_score_fit, beagle_eval, the serving loop and beagle_score_static always run every
+ * case. Process-wide setting.
+ *
+ * beagle_count_cases: while cases_run (a device array of P int64) is set, every following
+ * single-population scoring call with exactly P programs adds to cases_run[p] the fitness
+ * cases it ran for program p (N with the early exit off; fewer for invalid programs with it
+ * on, and 0 for malformed ones). Costs one atomic add per program and tile. NULL turns it off.
+ * BEAGLE_ERR_ARG for a non-null array with P <= 0.
+ */
+beagle_status beagle_set_invalid_early_exit(int32_t enable);
+beagle_status beagle_count_cases(int64_t *cases_run, int64_t P);
 beagle_status beagle_kernel_timing(int32_t enable);
 beagle_status beagle_kernel_time(double *total_ms, int64_t *launches);
 

@@ -88,6 +88,8 @@ _SIGNATURES = {
     "beagle_set_launch_config": ([_vp], _i32),
     "beagle_get_launch_config": ([_vp], _i32),
     "beagle_measure_op_rates": ([_vp, _i32, ctypes.c_double, _vp], _i32),
+    "beagle_set_invalid_early_exit": ([_i32], _i32),
+    "beagle_count_cases": ([_vp, _i64], _i32),
     "beagle_kernel_timing": ([_i32], _i32),
     "beagle_kernel_time": ([_vp, _vp], _i32),
     "beagle_last_error": ([], ctypes.c_char_p),
@@ -317,6 +319,20 @@ def measure_op_rates(seconds_hint: float = 1.0, stream=None) -> dict:
     rates = (ctypes.c_double * 16)()
     check(lib().beagle_measure_op_rates(rates, 16, seconds_hint, _stream_handle(stream)))
     return {i: float(rates[i]) for i in range(16) if rates[i] > 0}
+
+
+def set_invalid_early_exit(enable: bool):
+    """beagle_set_invalid_early_exit: stop evaluating a program once a case makes it invalid."""
+    check(lib().beagle_set_invalid_early_exit(1 if enable else 0))
+
+
+def count_cases(cases_run=None):
+    """beagle_count_cases: add each program's evaluated cases to cases_run (a CUDA int64
+    tensor of P), or stop counting (None)."""
+    if cases_run is None:
+        check(lib().beagle_count_cases(None, 0))
+    else:
+        check(lib().beagle_count_cases(_ptr(cases_run), int(cases_run.numel())))
 
 
 def kernel_timing(enable: bool):

@@ -96,6 +96,12 @@ struct JobDev {
     uint2 *packed;
     const uint32_t *poff;
     uint32_t *pmeta;
+    // Optional [P] flags, zero at launch: program p was found invalid on some tile (MSE kind
+    // only). A later tile of p then stores the invalid flag without running it. Null: every
+    // case of every tile runs (the early exits are off).
+    uint8_t *known_invalid;
+    // Optional [P] counters: the fitness cases each program's evaluation ran are added.
+    int64_t *cases_run;
 };
 
 // Packer result of a pre-packed program: bits 0-15 the handler count, then the flags.

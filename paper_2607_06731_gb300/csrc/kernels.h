@@ -70,6 +70,10 @@ cudaError_t launch_pack(const LaunchParams<MAXJ> &prm, int precision, cudaStream
 
 // Opt-in CUDA-event timing of scoring-kernel launches (beagle_kernel_timing).
 bool timing_enabled();
+// beagle_set_invalid_early_exit's setting, and beagle_count_cases' device array for a
+// single-job launch of P programs (else null).
+bool early_exit_enabled();
+int64_t *case_counter(int64_t P);
 void timing_begin(cudaStream_t s, void **token);
 void timing_end(cudaStream_t s, void *token);
 

@@ -77,6 +77,24 @@ bool timing_enabled() {
     return g_timing;
 }
 
+// ---------------------------------------------------------------- early exit, case counts
+namespace {
+std::mutex g_emu;
+bool g_early_exit = true;
+int64_t *g_cases_run = nullptr;
+int64_t g_cases_P = 0;
+}
+
+bool early_exit_enabled() {
+    std::lock_guard<std::mutex> lk(g_emu);
+    return g_early_exit;
+}
+
+int64_t *case_counter(int64_t P) {
+    std::lock_guard<std::mutex> lk(g_emu);
+    return g_cases_run && g_cases_P == P ? g_cases_run : nullptr;
+}
+
 void timing_begin(cudaStream_t s, void **token) {
     EvPair p;
     cudaEventCreate(&p.a);
@@ -130,6 +148,20 @@ beagle_status beagle_measure_op_rates(double *rates, int32_t n_rates, double sec
     cudaFreeAsync(sink, s);
     e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_fail(e, "measure_op_rates");
+    return BEAGLE_OK;
+}
+
+beagle_status beagle_set_invalid_early_exit(int32_t enable) {
+    std::lock_guard<std::mutex> lk(g_emu);
+    g_early_exit = enable != 0;
+    return BEAGLE_OK;
+}
+
+beagle_status beagle_count_cases(int64_t *cases_run, int64_t P) {
+    if (cases_run && P <= 0) return fail(BEAGLE_ERR_ARG, "count_cases: P must be positive");
+    std::lock_guard<std::mutex> lk(g_emu);
+    g_cases_run = cases_run;
+    g_cases_P = cases_run ? P : 0;
     return BEAGLE_OK;
 }
 

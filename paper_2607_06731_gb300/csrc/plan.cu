@@ -69,8 +69,9 @@ beagle_status enqueue(const std::vector<Planned> &jobs, size_t b, size_t e, int 
                       bool sort, cudaStream_t s) {
     LaunchParams<MAXJ> prm;
     std::memset(&prm, 0, sizeof prm);
-    // header (work counters, error word, deep counts), then per job: partials, the
-    // length order (when sorting) and the list of programs deeper than the fast pass's stack
+    // header (work counters, error word, deep counts), the sort's totals, the known-invalid
+    // flags, the sort's histograms, then per job: partials, the length order (when sorting)
+    // and the list of programs deeper than the fast pass's stack
     size_t scratch = kHdrBytes;
     // (when sorting, also the packed-token buffer, its offsets and the packer results)
     auto pack_cap = [](int64_t P) {
@@ -96,12 +97,15 @@ beagle_status enqueue(const std::vector<Planned> &jobs, size_t b, size_t e, int 
         }
     const size_t totals_bytes = up256(sizeof(int32_t) * (kMaxLen + 2) * norder);
     const size_t hist_bytes = up256(sizeof(int32_t) * (kMaxLen + 2) * nchunks);
-    scratch += totals_bytes + hist_bytes;
+    // each job's known-invalid flags (a byte per program, zeroed with the header)
+    size_t flags_bytes = 0;
+    for (size_t i = b; i < e; ++i) flags_bytes += up256(static_cast<size_t>(jobs[i].dev.P));
+    scratch += totals_bytes + flags_bytes + hist_bytes;
     char *base = nullptr;
     cudaError_t err = cudaMallocAsync(reinterpret_cast<void **>(&base), scratch, s);
     if (err != cudaSuccess)
         return fail(BEAGLE_ERR_OOM, "scratch of %zu bytes: %s", scratch, cudaGetErrorString(err));
-    err = cudaMemsetAsync(base, 0, kHdrBytes + totals_bytes, s);
+    err = cudaMemsetAsync(base, 0, kHdrBytes + totals_bytes + flags_bytes, s);
     if (err != cudaSuccess) {
         cudaFreeAsync(base, s);
         return cuda_fail(err, "scratch memset");
@@ -111,6 +115,8 @@ beagle_status enqueue(const std::vector<Planned> &jobs, size_t b, size_t e, int 
     char *cur = base + kHdrBytes;
     int32_t *order_totals = reinterpret_cast<int32_t *>(cur);
     cur += totals_bytes;
+    uint8_t *flags = reinterpret_cast<uint8_t *>(cur);
+    cur += flags_bytes;
     int32_t *order_hist = reinterpret_cast<int32_t *>(cur);
     cur += hist_bytes;
     int64_t items = 0;
@@ -120,6 +126,9 @@ beagle_status enqueue(const std::vector<Planned> &jobs, size_t b, size_t e, int 
     for (size_t i = b; i < e; ++i, ++nj) {
         prm.maps[nj] = *jobs[i].map;
         prm.jobs[nj] = jobs[i].dev;
+        prm.jobs[nj].known_invalid = early_exit_enabled() ? flags : nullptr;
+        flags += up256(static_cast<size_t>(jobs[i].dev.P));
+        if (MAXJ == 1) prm.jobs[nj].cases_run = case_counter(jobs[i].dev.P);
         prm.jobs[nj].partials = reinterpret_cast<uint32_t *>(cur);
         cur += up256(jobs[i].part_bytes);
         prm.jobs[nj].deep_list = reinterpret_cast<int32_t *>(cur);

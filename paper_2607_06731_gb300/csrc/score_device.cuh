@@ -349,6 +349,15 @@ __device__ __forceinline__ int process_program_kind(const JobDev &J, int64_t q, 
     using Sum = typename SumOf<T>::type;
     constexpr int CH = 32 * K;
     constexpr bool kPtx = sizeof(T) == 4 && (K == 4 || K == 8);   // the inline-PTX loops
+    // MSE / 1 - r^2 without per-case outputs: a tile with an invalid case is invalid whatever
+    // its other cases hold (it stores only its flag). So no pass runs after the first that
+    // finds one (nor any, for a folded constant that is invalid), and once some tile has found
+    // the program invalid its later tiles store the flag without running it (the flag is
+    // loaded here, its latency covered by the token copy below; L2, not L1, so that the other
+    // SMs' stores are seen). The paper's fitness functions count invalid cases and run them all;
+    // so does every launch whose flags array is null (beagle_set_invalid_early_exit(0)).
+    const bool stop_at_invalid = !FIT && J.fout == nullptr && J.known_invalid != nullptr;
+    const bool known_bad = stop_at_invalid && __ldcg(J.known_invalid + p) != 0;
     Packed pk;
     bool have = false;
     if constexpr (D == kDepthFast) {
@@ -412,10 +421,13 @@ __device__ __forceinline__ int process_program_kind(const JobDev &J, int64_t q, 
 
     TileValues<T, K> vals;
     vals.buf = fbuf;
-    bool anybad = pk.const_bad;
+    bool anybad = pk.const_bad || known_bad;
+    int c_run = 0;   // cases the passes ran (a pass runs CH cases, the last one fewer)
     if constexpr (sizeof(T) == 4 && K == 8) {
         static_assert(CH == kBox, "a pass of the 8-case loop is one staged box");
         for (int c0 = 0; c0 < nval; c0 += CH) {
+            if (stop_at_invalid && __any_sync(kFull, anybad)) break;
+            c_run = c0 + CH;
             const float *xrow = xs + (c0 / kBox) * rows * kBox + lane * 4;
             float f[8];
             bool bad[8];
@@ -430,6 +442,8 @@ __device__ __forceinline__ int process_program_kind(const JobDev &J, int64_t q, 
         }
     } else {
         for (int c0 = 0; c0 < nval; c0 += CH) {
+            if (stop_at_invalid && __any_sync(kFull, anybad)) break;
+            c_run = c0 + CH;
             const float *xrow = xs + (c0 / kBox) * rows * kBox + (c0 % kBox) + lane * K;
             T f[K];
             bool bad[K];
@@ -450,6 +464,9 @@ __device__ __forceinline__ int process_program_kind(const JobDev &J, int64_t q, 
         }
     }
     anybad = __any_sync(kFull, anybad);
+    if (J.cases_run != nullptr && lane == 0)
+        atomicAdd(reinterpret_cast<unsigned long long *>(J.cases_run + p),
+                  static_cast<unsigned long long>(min(c_run, nval)));
     __syncwarp();
     const int halves = (nval + 127) / 128;
     if (J.fout) {   // per-case outputs requested (beagle_eval)
@@ -467,7 +484,10 @@ __device__ __forceinline__ int process_program_kind(const JobDev &J, int64_t q, 
         return 0;
     }
     if (anybad) {
-        if (lane == 0) *field(kTileFlags) = TF_INVALID;
+        if (lane == 0) {
+            *field(kTileFlags) = TF_INVALID;
+            if (stop_at_invalid && !known_bad) J.known_invalid[p] = 1;
+        }
         return 0;
     }
 

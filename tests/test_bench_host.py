@@ -66,3 +66,35 @@ def test_folded_op_counts_match_a_sequential_fold():
                     want[op] += 1
     assert np.array_equal(got, want)
     assert want.sum() > 0
+
+
+def test_case_weights_scale_the_executed_work():
+    """The roofline's units and the executed node count follow each program's share of the
+    cases it ran (beagle_count_cases): every case gives the unweighted counts; a program that
+    ran half its cases counts half; one that ran none, nothing."""
+    rng = np.random.default_rng(8)
+    progs = S.gen_programs(rng, 300, 3, 40, 3)
+    N = 1 << 15                                    # P N below 2^24: no folding
+    ones = np.ones(progs.P)
+    assert np.array_equal(bench.op_counts(progs, ones), bench.op_counts(progs))
+    assert np.allclose(bench.folded_op_counts(progs, ones), bench.folded_op_counts(progs))
+    full = bench.algorithmic_units([(progs, N)], folded=True)
+    same = bench.algorithmic_units([(progs, N, ones)], folded=True)
+    half = bench.algorithmic_units([(progs, N, 0.5 * ones)], folded=True)
+    for k in full:
+        assert np.isclose(same[k], full[k]) and np.isclose(half[k], 0.5 * full[k])
+    w = np.zeros(progs.P)
+    w[0] = 1.0
+    one = bench.algorithmic_units([(progs, N, w)], folded=False)
+    alone = bench.algorithmic_units([(progs.subset(np.array([0])), N)], folded=False)
+    for k in one:
+        assert np.isclose(one[k], alone[k])
+    cases = np.full(progs.P, N, np.int64)
+    cases[: progs.P // 2] = N // 4
+    info = bench.work_info(progs, N, cases, ms=2.0)
+    L = progs.lengths.astype(np.float64)
+    want = (L[: progs.P // 2].sum() * (N // 4) + L[progs.P // 2:].sum() * N)
+    assert np.isclose(info["executed_node_evals_per_step"], want)
+    assert np.isclose(info["executed_case_fraction"], cases.sum() / (progs.P * N))
+    assert np.isclose(info["executed_gpops"], want / 2e-3 / 1e9)
+    assert bench.work_info(progs, N)["executed_node_evals_per_step"] == L.sum() * N
