@@ -424,8 +424,8 @@ beagle_status beagle_measure_op_rates(double *rates, int32_t n_rates, double sec
  * its later tiles are not run. The results are the same bits either way; the work done, and
  * so the time, depends on how many programs are invalid and where. enable = 0 turns this off
  * (every case of every program runs) for the calls that follow, 1 turns it back on.
- * beagle_score_fit, beagle_eval, the serving loop and beagle_score_static always run every
- * case. Process-wide setting.
+ * The serving loop takes the setting when a request is submitted. beagle_score_fit,
+ * beagle_eval and beagle_score_static always run every case. Process-wide setting.
  *
  * beagle_count_cases: while cases_run (a device array of P int64) is set, every following
  * single-population scoring call with exactly P programs adds to cases_run[p] the fitness

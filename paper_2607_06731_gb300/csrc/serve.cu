@@ -202,16 +202,18 @@ beagle_status stage_request(beagle_server *s, Request &r, ServeJob *out) {
     r.tiles = tiles;
     const size_t b_part = up256(static_cast<size_t>(kNumFields) * 4 * tiles * r.P);
     const size_t b_in = up256(r.in_bytes), b_td = up256(4 * static_cast<size_t>(r.P)),
+                 b_flags = up256(static_cast<size_t>(r.P)),
                  b_deep = up256(4 * static_cast<size_t>(r.P)), b_cnt = 256;
-    const size_t total = b_in + b_part + b_td + b_deep + b_cnt;
+    const size_t total = b_in + b_part + b_td + b_flags + b_deep + b_cnt;
     cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&r.dev), total, s->cstream);
     if (e != cudaSuccess) {
         r.dev = nullptr;
         return fail(BEAGLE_ERR_OOM, "serve: device buffers: %s", cudaGetErrorString(e));
     }
-    char *in = r.dev, *part = in + b_in, *td = part + b_part, *deep = td + b_td, *cnt = deep + b_deep;
+    char *in = r.dev, *part = in + b_in, *td = part + b_part, *flags = td + b_td,
+         *deep = flags + b_flags, *cnt = deep + b_deep;
     e = cudaMemcpyAsync(in, r.host_in, r.in_bytes, cudaMemcpyHostToDevice, s->cstream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(td, 0, b_td, s->cstream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(td, 0, b_td + b_flags, s->cstream);   // and flags
     if (e == cudaSuccess) e = cudaMemsetAsync(cnt, 0, b_cnt, s->cstream);
     if (e != cudaSuccess) return cuda_fail(e, "serve: copy in");
     void *out_dev = nullptr;
@@ -238,6 +240,8 @@ beagle_status stage_request(beagle_server *s, Request &r, ServeJob *out) {
     J.deep_list = reinterpret_cast<int32_t *>(deep);
     J.deep_count = reinterpret_cast<int32_t *>(cnt + 128);
     J.kind = kFitMse;
+    // the early exit on invalid programs (the request's known-invalid flags, zeroed above)
+    J.known_invalid = early_exit_enabled() ? reinterpret_cast<uint8_t *>(flags) : nullptr;
     std::memset(out, 0, sizeof *out);
     out->map = r.ds->map;
     out->dev = J;
