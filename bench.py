@@ -482,17 +482,18 @@ def cpu_baseline(pr, seconds: float, threads: int = 0):
     rng = np.random.default_rng(1234)
     mean_len = float(pr.programs.lengths.mean())
     n = int(min(pr.programs.P, max(2, min(200, 2e8 / (mean_len * pr.N)))))
-    idx = rng.choice(pr.programs.P, n, replace=False)
-    sub = pr.programs.subset(idx)
-    t0 = time.perf_counter()
-    oracle.score_programs(sub, pr.X, pr.y, "fp64", nthreads=threads)
-    dt = max(time.perf_counter() - t0, 1e-6)
-    n2 = int(min(pr.programs.P, max(n, n * seconds / dt)))
-    idx = rng.choice(pr.programs.P, n2, replace=False)
-    sub = pr.programs.subset(idx)
-    t0 = time.perf_counter()
-    oracle.score_programs(sub, pr.X, pr.y, "fp64", nthreads=threads)
-    dt = time.perf_counter() - t0
+    # sample sizes scaled from the previous run's time until a run takes at least half the
+    # target (the first, small run also pays the thread pool's start)
+    n2 = n
+    for _ in range(4):
+        idx = rng.choice(pr.programs.P, n2, replace=False)
+        sub = pr.programs.subset(idx)
+        t0 = time.perf_counter()
+        oracle.score_programs(sub, pr.X, pr.y, "fp64", nthreads=threads)
+        dt = max(time.perf_counter() - t0, 1e-6)
+        if dt >= 0.5 * seconds or n2 >= pr.programs.P:
+            break
+        n2 = int(min(pr.programs.P, max(n2 + 1, n2 * seconds / dt)))
     evals = int(sub.lengths.sum()) * pr.N
     out = {"value": evals / dt / 1e9, "unit": "GPoPs", "cores": oracle.threads(),
            "kind": "oracle",
@@ -1072,13 +1073,16 @@ def handler_programs():
 def run_handlers(args):
     """One launch per (handler, n) for n = 8 and 15; prints each launch's interpreter steps
     (tokens after leaf + binary fusion, plus END, per 128-case pass, over all programs). Under
-    ncu, (instructions(15) - instructions(8)) / (steps(15) - steps(8)) is the handler's cost."""
+    ncu, (instructions(15) - instructions(8)) / (steps(15) - steps(8)) is the handler's cost.
+    The early exit on invalid programs is off: a chain of 15 exps or squares overflows, and
+    every case must still run for the count to hold."""
     import torch
     from paper_2607_06731_gb300 import beagle, synth as S
     X = np.random.default_rng(0).uniform(0.5, 1.5, (3, HANDLER_N)).astype(np.float32)
     y = (X[0] + X[1]).astype(np.float32)
     ds = beagle.Dataset(X, y)
     beagle.set_launch_config(cases_per_lane=4, tile=512, keep_order=1)
+    beagle.set_invalid_early_exit(False)
     lines = []
     try:
         for name, mk in handler_programs().items():
@@ -1095,6 +1099,7 @@ def run_handlers(args):
                 lines.append({"handler": name, "n": n, "steps": steps})
                 print(json.dumps(lines[-1]), flush=True)
     finally:
+        beagle.set_invalid_early_exit(True)
         beagle.reset_launch_config()
         ds.release()
     return 0
