@@ -97,3 +97,34 @@ def test_early_exit_same_bits_and_case_counts(cases, keep_order):
 def test_case_counter_needs_a_positive_population():
     with pytest.raises(beagle.BeagleError):
         beagle.check(beagle.lib().beagle_count_cases(1, 0))
+
+
+@pytest.mark.parametrize("precision", ["fp32c", "fp64"])
+def test_serving_early_exit_same_bits(precision):
+    """The serving loop stops invalid programs early too (the setting taken per request): the
+    served records are the bits served with every case run, and beagle_score's."""
+    rng = np.random.default_rng(620)
+    d, N = 3, 3000
+    X = rng.uniform(-6, 6, (d, N)).astype(np.float32)
+    X[0] = np.sort(X[0])
+    y = (X[0] * X[1] + np.sin(X[2])).astype(np.float32)
+    progs = _population(rng, d)
+    ds = beagle.Dataset(X, y)
+    try:
+        ref, _ = _score(beagle.DevicePrograms(progs), ds, progs.P, precision, True)
+        served = []
+        for early in (True, False):
+            beagle.set_invalid_early_exit(early)
+            srv = beagle.Server(precision=precision)
+            try:
+                served.append(beagle.unpack_fitness(srv.wait(srv.submit(progs, ds),
+                                                             timeout_us=60_000_000)))
+            finally:
+                srv.destroy()
+                beagle.set_invalid_early_exit(True)
+        for got in served:
+            for a, b in zip(got, ref):
+                assert np.array_equal(a, b, equal_nan=True)
+        assert np.any(ref[2] & beagle.FLAG_INVALID)
+    finally:
+        ds.release()
