@@ -158,8 +158,8 @@ beagle_status beagle_dataset_info(int32_t dataset_id, int64_t *N, int32_t *d, do
  * token finds its operands, the stack never holds more than max_depth values, inputs exist,
  * COPY and PASTE pair up, exactly one value remains, and 1 <= length <= BEAGLE_MAX_LENGTH. All
  * pointers are host pointers. Returns BEAGLE_ERR_PROGRAM and the index of the first bad
- * program in *first_bad (if not NULL), else BEAGLE_OK and -1. (max_depth and the 64-bit index
- * extend the SURVEY's signature: the GPU's limit and the paper's StackSize differ.)
+ * program in *first_bad (if not NULL), else BEAGLE_OK and -1. (max_depth: the GPU's depth limit
+ * and the paper's StackSize differ; the index is 64-bit like P.)
  */
 beagle_status beagle_validate_programs(const uint8_t *programs, const int64_t *offsets,
                                        const int32_t *lengths, int64_t P, int32_t d,
@@ -189,7 +189,9 @@ beagle_status beagle_validate_programs_ex(const uint8_t *programs, const int64_t
  * longer than BEAGLE_MAX_LENGTH) gets BEAGLE_FLAG_MALFORMED instead of a fitness.
  * Asynchronous on stream; the call uses stream-ordered scratch memory that it frees itself.
  * Results are deterministic: the same program and dataset give the same bits in any
- * population and any batch.
+ * population and any batch. A program found invalid on one case is not evaluated on its
+ * remaining cases (see beagle_set_invalid_early_exit): the results are the same bits, the
+ * work done depends on how many programs are invalid.
  */
 beagle_status beagle_score(const uint8_t *programs, const int64_t *offsets,
                            const int32_t *lengths, const float *consts, int64_t P,
