@@ -147,3 +147,14 @@ def test_serve_api_argument_checks_without_a_gpu():
     assert ctypes.sizeof(beagle.ServeConfig) == 24
     assert ctypes.sizeof(beagle.Request) == 56
     assert ctypes.sizeof(beagle.ServeStats) == 10 * 8 + 4 * 8
+
+
+def test_early_exit_and_case_counter_settings_without_a_gpu():
+    """beagle_set_invalid_early_exit and beagle_count_cases are host settings: they take no
+    device work; a counter array needs a positive population size."""
+    L = beagle.lib()
+    assert L.beagle_set_invalid_early_exit(0) == 0
+    assert L.beagle_set_invalid_early_exit(1) == 0
+    assert L.beagle_count_cases(1, 0) == -1          # BEAGLE_ERR_ARG
+    assert L.beagle_count_cases(1, -5) == -1
+    assert L.beagle_count_cases(None, 0) == 0        # off
