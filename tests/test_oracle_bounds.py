@@ -1,6 +1,8 @@
 """Pins of the oracle's running error bound (no GPU): a device model that perturbs every
-sin, cos, exp and log result by up to the documented ulp error must land inside the bound,
-and programs without transcendentals have a zero bound."""
+sin, cos, exp and log result by up to the documented ulp error must land inside the bound;
+programs without transcendentals have a zero per-case bound, and their fitness bound (the
+aggregation slack alone) covers the same outputs aggregated by tiles in the device's fp64
+order."""
 from __future__ import annotations
 
 import math
@@ -99,3 +101,58 @@ def test_fitness_bound_covers_perturbed_fitness():
             assert abs(mg - m[p]) <= bm[p] * (1 + 1e-6) + 1e-12 * abs(m[p]), p
             if not (fl[p] & oracle.F_DEGENERATE) and np.any(g != g[0]):
                 assert abs(rg - r[p]) <= br[p] * (1 + 1e-6) + 1e-12, p
+
+
+def _tiled_omr2(f, y, tile=512):
+    """1 - r^2 aggregated the way a tiled device does it in fp64, in an order unlike the
+    oracle's: per tile a two-pass mean m_t and the sums of d = f - m_t, d^2 and d (y - ybar),
+    plain fp64; the tiles merged around fbar = sum (n_t m_t + sum d) / N with
+    S_ff = sum (sum d^2 + 2 (m_t - fbar) sum d + n_t (m_t - fbar)^2) and
+    S_fy = sum (sum d (y - ybar) + (m_t - fbar) sum (y - ybar))."""
+    f = np.asarray(f, np.float64)
+    yd = np.asarray(y, np.float64)
+    yc = yd - yd.sum() / len(yd)
+    tiles = []
+    for a in range(0, len(f), tile):
+        ft, yt = f[a:a + tile], yc[a:a + tile]
+        m = ft.sum() / len(ft)
+        d = ft - m
+        tiles.append((len(ft), m, d.sum(), float(np.dot(d, d)), float(np.dot(d, yt)), yt.sum()))
+    fbar = sum(n * m + sd for n, m, sd, _, _, _ in tiles) / len(f)
+    sff = sum(sdd + 2.0 * (m - fbar) * sd + n * (m - fbar) ** 2 for n, m, sd, sdd, _, _ in tiles)
+    sfy = sum(sdy + (m - fbar) * sy for _, m, _, _, sdy, sy in tiles)
+    syy = float(np.dot(yc, yc))
+    return 1.0 - sfy * sfy / (sff * syy)
+
+
+def test_aggregation_slack_covers_a_tiled_fp64_aggregation():
+    """For programs without transcendentals every per-case bound is 0 (both sides round the
+    same correctly rounded operations), so the 1 - r^2 bound is the aggregation slack alone:
+    it must cover the same outputs aggregated by tiles in another fp64 order -- including
+    outputs that differ only in their last bits, where the rounding of the mean dominates."""
+    rng = np.random.default_rng(31)
+    N = 3000
+    X = rng.uniform(-2, 2, (2, N)).astype(np.float32)
+    y = (X[0] * X[1] + 0.3 * X[0]).astype(np.float32)
+    progs = S.gen_programs(rng, 300, 3, 30, 2, unary=(S.SQUARE,))
+    C, L0 = S.CONST, S.LOAD0
+    # outputs 1 + x0 1e-14 and 1e6 + x1: variation only in the last bits of the fp64 outputs
+    near = S.from_token_lists([[(L0, 0.0), (C, 1e-14), (S.MUL, 0.0), (C, 1.0), (S.ADD, 0.0)],
+                               [(L0 + 1, 0.0), (C, 1e6), (S.ADD, 0.0)]])
+    for pop in (progs, near):
+        m, r, fl, bm, br = oracle.score_bound(pop, X, y, "fp64")
+        checked = 0
+        for p in range(pop.P):
+            if fl[p] & (oracle.F_INVALID | oracle.F_DEGENERATE | oracle.F_MALFORMED):
+                continue
+            ops, cs = pop.program(p)
+            f, _ = oracle.eval_program(ops, cs, X, "fp64")
+            if np.all(f == f[0]):
+                assert br[p] == 0.0
+                continue
+            assert br[p] > 0.0                      # the slack, per-case bounds being 0
+            for tile in (512, 256):
+                got = _tiled_omr2(f, y, tile)
+                assert abs(got - r[p]) <= br[p], (p, tile, got, r[p], br[p])
+            checked += 1
+        assert checked >= (2 if pop is near else 100)
