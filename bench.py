@@ -642,6 +642,20 @@ def score_population(beagle, torch, pr, stream, flush, steps, warmup, clocks=Non
             "kernel_s": kern_avg, "tuned": tuned, "cases_run": cases_run}
 
 
+# DRAM bytes (read + write) of one headline fast-pass launch at P = 2,000 programs, measured
+# with ncu on the current kernel (dram__bytes_read.sum + dram__bytes_write.sum).
+C3_TRAFFIC_P2000 = 167.66e6 + 148.59e6
+
+
+def headline_traffic(P: int):
+    """The headline kernel's DRAM traffic per launch, scaled from the P = 2,000 capture: both
+    parts grow with P (input tiles staged once per program group and tile, 44 bytes of
+    partials per program and tile)."""
+    return {"traffic": C3_TRAFFIC_P2000 * P / 2000.0,
+            "traffic_basis": ("dram__bytes_read.sum + dram__bytes_write.sum of one fast-pass "
+                              "launch at P = 2,000 (ncu), scaled by P / 2,000")}
+
+
 def roofline_of(ev, r, pr, sm_mhz, sms, rates):
     """The roofline entry of one timed population (executed operators and cases)."""
     folds = launch_folds(pr.programs.P, pr.N)
@@ -841,7 +855,8 @@ def run_headline(args, rank, world, local):
         "fp32c_vs_fp64_speedup": statistics.median(r["ms64"]) / statistics.median(ms),
         "fp32c_vs_fp64_path": fp32_vs_fp64_path(r["g32"], r["g64"]),
         "parity": parity,
-        "roofline": roofline_of(ev, r, pr, sm_mhz, sms, rates),
+        "roofline": {**roofline_of(ev, r, pr, sm_mhz, sms, rates),
+                     **headline_traffic(pr.programs.P)},
         "cpu_baseline": cpu,
         "e2e": {"value": ev / e2e["seconds"] / 1e9, "unit": "GPoPs",
                 "h2d_bytes_per_step": e2e["h2d"], "d2h_bytes_per_step": e2e["d2h"]},
